@@ -1,0 +1,155 @@
+/*
+ * liblbm: single-GPU (sm_103a) lattice-Boltzmann stream-and-collide with the
+ * recursive-regularized (RR) collision of Coreixas, Wissocq, Puigt, Boussuge &
+ * Sagaut, "Recursive regularization step for high-order lattice Boltzmann
+ * methods" (arXiv 1704.04413), on the D2Q9, D2V17 and D2V37 lattices of its
+ * Tab. I, with BGK (Sec. III.A) and projection regularization (PR, Sec. II.E)
+ * as comparison modes.
+ *
+ * Conventions shared by every call:
+ *  - Lattice units (Delta x = Delta t = 1, Sec. III.A).  Velocities are the
+ *    integer on-grid vectors of Tab. I; cs^2 is the lattice constant.
+ *  - Fields are row-major [ny][nx] arrays of double (x fastest).  Populations
+ *    exchanged with the caller are [V][ny][nx] doubles in the library's
+ *    velocity order (lbm_lattice_info).
+ *  - theta is the temperature T/T0 in units of the lattice reference
+ *    temperature (p = rho cs^2 theta).
+ *  - `on_device` = 0: pointers are host memory (pageable or pinned); the call
+ *    copies through the context's stream and returns when the data is usable.
+ *    `on_device` = 1: pointers are device memory on the context's GPU (for
+ *    example a torch tensor's data_ptr()); the call only enqueues work on the
+ *    context's stream.
+ *  - Return value: LBM_OK (0) or a negative LBM_E* code; no call aborts the
+ *    process.  lbm_strerror() names a code; lbm_last_error() gives the detail
+ *    of a context's last failure.
+ *  - The caller owns every array it passes; the library copies what it needs.
+ *    The library owns the device populations of a context.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* lattices (Tab. I) */
+#define LBM_D2Q9 0
+#define LBM_D2V17 1
+#define LBM_D2V37 2
+
+/* collision models */
+#define LBM_BGK 0 /* f* = f - (f - f^(0)) / tau                      (Sec. III.A) */
+#define LBM_PR 1  /* projected a1^(n), n = 2..N, Eq. RegularizedCollision (Sec. II.E) */
+#define LBM_RR 2  /* a1^(2) projected, a1^(n>2) recursive (Eqs. MalaspinasRecursiveRelation,
+                     RecursiveRelation_ThermalCase; App. C) */
+
+/* boundary of an axis */
+#define LBM_PERIODIC 0
+#define LBM_ZERO_GRADIENT 1 /* a pulled source outside the domain reads the nearest edge cell */
+
+/* population storage / compute precision */
+#define LBM_F64 0
+#define LBM_F32 1
+#define LBM_F16_SHIFT 2  /* binary16 of g_i = (f_i / w_i - rho0) * s */
+#define LBM_BF16_SHIFT 3 /* bfloat16 of the same shifted deviation */
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)
+#define LBM_ENOMEM (-2)
+#define LBM_ECUDA (-3)
+#define LBM_EUNSTABLE (-4)
+#define LBM_ETIMEOUT (-5)
+#define LBM_EIO (-6)
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef struct {
+  int lattice;       /* LBM_D2Q9, LBM_D2V17, LBM_D2V37 */
+  int hermite_order; /* N of the equilibrium f^(0),N (Sec. II.C): 2..lattice maximum (4, 3, 4) */
+  int reg_order;     /* N of f^(1),N (Sec. II.D): 2..lattice maximum; 0 = lattice maximum */
+  int collision;     /* LBM_BGK, LBM_PR, LBM_RR */
+  int thermal;       /* 1: theta from the energy moment (D2V37 only); 0: theta = 1 */
+  int nx, ny;        /* grid, each >= 1 */
+  double nu;         /* kinematic viscosity; used when tau <= 0: tau = nu / cs^2 + 1/2 */
+  double tau;        /* relaxation time of the discrete scheme (the shifted tau-bar of Sec. III.A), > 1/2 */
+  int bc_x, bc_y;    /* LBM_PERIODIC or LBM_ZERO_GRADIENT */
+  int storage;       /* LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT */
+  int compute;       /* LBM_F64 (requires storage LBM_F64) or LBM_F32 (any other storage) */
+  double rho0;       /* shifted storage reference density; 0 = 1 */
+  double store_scale;/* shifted storage scale s, a power of two; 0 = 1 */
+  void *stream;      /* cudaStream_t all work of the context is issued on; NULL = legacy default stream */
+} lbm_params;
+
+/* Lattice description in the library's velocity order (Tab. I).  Any output
+ * pointer may be NULL; cx, cy, w must hold at least 37 entries.
+ * Returns LBM_EINVAL for an unknown lattice. */
+int lbm_lattice_info(int lattice, int *V, int *cx, int *cy, double *w, double *cs2);
+
+/* Validate `p`, pick the kernels, allocate two population buffers of
+ * V * ny * pitch elements on the current CUDA device.  No computation.
+ * Errors: LBM_EINVAL (any field out of range, including tau <= 1/2,
+ * thermal on a lattice other than D2V37, an order above the lattice's basis),
+ * LBM_ENOMEM, LBM_ECUDA.  *out is NULL on failure. */
+int lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Release the context and its device memory (NULL is accepted). */
+void lbm_destroy(lbm_ctx *c);
+
+/* Initial state f = f^(0),N(rho, u, theta) + f^(1) (Sec. III.B).  f^(1) is
+ * built from the Chapman-Enskog a1^(2) of the supplied velocity gradients
+ * (App. A: -tau rho cs^2 theta (S - (2/D) div u delta) thermal, -tau rho cs^2 S
+ * isothermal) and the recursions for higher orders; grad_u = NULL gives
+ * f = f^(0).  grad_u is [4][ny][nx] = d ux/dx, d ux/dy, d uy/dx, d uy/dy.
+ * theta may be NULL (theta = 1).  Resets the step counter. */
+int lbm_init(lbm_ctx *c, const double *rho, const double *ux, const double *uy, const double *theta,
+             const double *grad_u, int on_device);
+
+/* Advance n >= 0 time steps.  Each step is one fused kernel: pull streaming
+ * (Sec. III.A, method of characteristics) then collision, double-buffered.
+ * Enqueued on the context's stream; does not synchronize. */
+int lbm_step(lbm_ctx *c, int n);
+
+/* Macroscopic fields of the current state: rho, ux, uy and theta
+ * (theta = 1 when isothermal); any output may be NULL. */
+int lbm_moments(lbm_ctx *c, double *rho, double *ux, double *uy, double *theta, int on_device);
+
+/* FP64 domain sums: out[0] mass, out[1..2] momentum, out[3] total energy
+ * (1/2 sum_i f_i |xi_i|^2), deterministic (fixed-order two-pass reduction).
+ * Synchronizes.  Returns LBM_EUNSTABLE (sums still written) when a sum is not
+ * finite. */
+int lbm_conservation(lbm_ctx *c, double out[4]);
+
+/* Flow diagnostics of Sec. III.B: out[0] = mean u^2, out[1] = std u^2,
+ * out[2] = mean enstrophy density omega^2/2, out[3] = its std, with omega from
+ * fourth-order centred differences (periodic wrap, clamped on zero-gradient
+ * axes).  Synchronizes; LBM_EUNSTABLE when a value is not finite. */
+int lbm_diagnostics(lbm_ctx *c, double out[4]);
+
+/* Decoded populations f[V][ny][nx] (double) of the current state, and the
+ * inverse (encodes into the storage format; rounding applies). */
+int lbm_get_populations(lbm_ctx *c, double *f, int on_device);
+int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
+
+/* Number of steps since the last lbm_init / lbm_set_populations / lbm_load. */
+long long lbm_step_count(const lbm_ctx *c);
+
+/* The relaxation time tau actually used (derived from nu when tau <= 0). */
+double lbm_tau(const lbm_ctx *c);
+
+/* Checkpoint: header (format tag, parameters, step count) and the raw stored
+ * populations.  lbm_load requires a file written by a context with the same
+ * lattice, grid, storage and collision parameters (LBM_EINVAL otherwise,
+ * LBM_EIO on read/write failure); the restored state is bit-identical. */
+int lbm_save(lbm_ctx *c, const char *path);
+int lbm_load(lbm_ctx *c, const char *path);
+
+/* Text of a status code / of the context's last failure. */
+const char *lbm_strerror(int code);
+const char *lbm_last_error(const lbm_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,331 @@
+// Per-cell arithmetic of the regularized lattice-Boltzmann step (Coreixas et
+// al., arXiv 1704.04413): moments (Sec. II.A), equilibrium Hermite
+// coefficients a0 (App. B, written out for 2D), off-equilibrium coefficients
+// a1 by projection (Sec. II.E) or by recursion (Eqs. MalaspinasRecursiveRelation
+// and RecursiveRelation_ThermalCase in the 2D form of App. C, Eq. a1Rec), the
+// thermal a1^(3) filtering of App. C (Eq. TempGradLBM) and the rebuild of
+// Eq. (GenRegCollision) with a single relaxation time.
+//
+// A 2D Hermite coefficient with a x-indices and b y-indices is kept as
+// X[a][b]; its tensor multiplicity A^(n) of App. C is folded into the factor
+// 1 / (a! b! cs^2(a+b)).  All lattice-dependent numbers are compile-time
+// constants (lattice.cuh); loops over populations and orders are unrolled.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lattice.cuh"
+
+#define LBM_CI(X) decltype(X)::value
+
+namespace lbm {
+
+enum { COLL_BGK = 0, COLL_PR = 1, COLL_RR = 2 };
+
+template <class Real>
+struct CollParams {
+  Real omega;  // 1 / tau
+  Real om1;    // 1 - 1 / tau
+  int neq;     // highest order of f^(0)
+  int nreg;    // highest order of f^(1)
+  Real rho0;   // shift of low-precision storage
+  Real s;      // scale of low-precision storage
+  Real inv_s;
+};
+
+// ---------------------------------------------------------------------------
+// Storage formats.  Plain formats hold f_i.  Shifted low-precision formats
+// hold g_i = (f_i / w_i - rho0) * s, i.e. the relative deviation from the
+// reference equilibrium w_i rho0, times a power of two s.
+// ---------------------------------------------------------------------------
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+  static constexpr bool SHIFTED = false;
+  __device__ static __forceinline__ double ld(const double* p) { return __ldg(p); }
+  __device__ static __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <>
+struct Store<float> {
+  static constexpr bool SHIFTED = false;
+  __device__ static __forceinline__ float ld(const float* p) { return __ldg(p); }
+  __device__ static __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+  static constexpr bool SHIFTED = true;
+  __device__ static __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  static constexpr bool SHIFTED = true;
+  __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// Equilibrium coefficients a0 (App. B recursion specialised to 2D):
+//   a0[a][b] = u_y a0[a][b-1] + (b-1) e a0[a][b-2]            (b > 0)
+//   a0[a][0] = u_x a0[a-1][0] + (a-1) e a0[a-2][0]
+// with e = cs^2 (theta - 1).
+// ---------------------------------------------------------------------------
+template <class L, bool THERMAL, class Real>
+__device__ __forceinline__ void equilibrium_coefficients(Real rho, Real ux, Real uy, Real e, Real (&A)[5][5]) {
+  A[0][0] = rho;
+  sfor<1, L::NMAX + 1>([&](auto N) {
+    constexpr int n = LBM_CI(N);
+    sfor<0, n + 1>([&](auto Aa) {
+      constexpr int a = LBM_CI(Aa);
+      constexpr int b = n - a;
+      if constexpr (L::keep(a, b)) {
+        if constexpr (b > 0) {
+          Real v = uy * A[a][b - 1];
+          if constexpr (THERMAL && b >= 2) v += Real(b - 1) * e * A[a][b - 2];
+          A[a][b] = v;
+        } else {
+          Real v = ux * A[a - 1][0];
+          if constexpr (THERMAL && a >= 2) v += Real(a - 1) * e * A[a - 2][0];
+          A[a][0] = v;
+        }
+      }
+    });
+  });
+}
+
+// Third-order a1 from a1^(2) (isothermal recursion, App. C Eq. a1Rec with no
+// temperature gradient), then fourth order by App. C (theta-dependent form).
+template <class L, bool THERMAL, class Real>
+__device__ __forceinline__ void a1_third_from_second(Real ux, Real uy, Real (&B)[5][5]) {
+  if constexpr (L::NMAX >= 3) {
+    B[3][0] = Real(3) * ux * B[2][0];
+    B[2][1] = Real(2) * ux * B[1][1] + uy * B[2][0];
+    B[1][2] = Real(2) * uy * B[1][1] + ux * B[0][2];
+    B[0][3] = Real(3) * uy * B[0][2];
+  }
+}
+template <class L, bool THERMAL, class Real>
+__device__ __forceinline__ void a1_fourth(Real ux, Real uy, Real e, Real (&B)[5][5]) {
+  if constexpr (L::NMAX >= 4) {
+    Real ex = -ux * ux, ey = -uy * uy;
+    if constexpr (THERMAL) {
+      ex += e;
+      ey += e;
+    }
+    const Real uxy = ux * uy;
+    B[4][0] = Real(4) * ux * B[3][0] + Real(6) * ex * B[2][0];
+    B[3][1] = Real(3) * ux * B[2][1] + uy * B[3][0] + Real(3) * ex * B[1][1] - Real(3) * uxy * B[2][0];
+    B[2][2] = Real(2) * (ux * B[1][2] + uy * B[2][1]) + ex * B[0][2] + ey * B[2][0] - Real(4) * uxy * B[1][1];
+    B[1][3] = Real(3) * uy * B[1][2] + ux * B[0][3] + Real(3) * ey * B[1][1] - Real(3) * uxy * B[0][2];
+    B[0][4] = Real(4) * uy * B[0][3] + Real(6) * ey * B[0][2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Rebuild: out_i = sum_{(a,b) kept} K_i He(a, cx_i) He(b, cy_i) C[a][b], with
+// K_i = w_i for plain storage and 1 for shifted storage (whose C carry the
+// factor s and whose w_i cancels).  Factorised by rows of equal cy:
+//   g[a](v) = sum_b He(b, v) C[a][b],   out_i = sum_a K_i He(a, cx_i) g[a](cy_i),
+// and g[a](+-v) = E +- O with E/O the even/odd-b parts.
+// ---------------------------------------------------------------------------
+template <class L, bool SHIFTED, class Real, class F>
+__device__ __forceinline__ void rebuild(const Real (&C)[5][5], F&& emit) {
+  constexpr double c2 = L::CS2;
+  constexpr int V = L::VMAX;
+  Real g[5][2 * V + 1];
+  sfor<0, V + 1>([&](auto VV) {
+    constexpr int v = LBM_CI(VV);
+    if constexpr (has_row<L>(v) || has_row<L>(-v)) {
+      sfor<0, L::NMAX + 1>([&](auto Aa) {
+        constexpr int a = LBM_CI(Aa);
+        if constexpr (L::keep(a, 0)) {
+        Real ev = Real(0), od = Real(0);
+        sfor<0, L::NMAX + 1 - a>([&](auto Bb) {
+          constexpr int b = LBM_CI(Bb);
+          constexpr double h = he(b, v, c2);
+          if constexpr (L::keep(a, b) && h != 0.0) {
+            if constexpr (b % 2 == 0)
+              ev += Real(h) * C[a][b];
+            else
+              od += Real(h) * C[a][b];
+          }
+        });
+        g[a][V + v] = ev + od;
+        if constexpr (v != 0) g[a][V - v] = ev - od;
+        }
+      });
+    }
+  });
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    constexpr int v = L::CY[i];
+    Real acc = Real(0);
+    sfor<0, L::NMAX + 1>([&](auto Aa) {
+      constexpr int a = LBM_CI(Aa);
+      constexpr double h = he(a, L::CX[i], c2) * (SHIFTED ? 1.0 : L::W[i]);
+      if constexpr (h != 0.0 && L::keep(a, 0)) acc += Real(h) * g[a][V + v];
+    });
+    emit(I, acc);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// One collision.  q holds the pulled populations in storage representation
+// (converted to Real) and receives the post-collision ones.
+// ---------------------------------------------------------------------------
+template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real>
+__device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P) {
+  constexpr double c2 = L::CS2;
+  // highest monomial order of f the mode needs
+  constexpr int PM = (COLL == COLL_PR) ? L::NMAX : (COLL == COLL_RR ? (THERMAL ? 3 : 2) : 1);
+
+  // --- monomial moments m[k][l] = sum_i f_i cx^k cy^l (Sec. II.A) ---
+  Real m[5][5];
+  sfor<0, 5>([&](auto K) {
+    constexpr int k = LBM_CI(K);
+    sfor<0, 5 - k>([&](auto Lq) {
+      constexpr int l = LBM_CI(Lq);
+      if constexpr (L::keep(k, l) && k + l <= PM) {
+        Real acc = Real(0);
+        sfor<0, L::Q>([&](auto I) {
+          constexpr int i = LBM_CI(I);
+          constexpr double c = ipow(L::CX[i], k) * ipow(L::CY[i], l) * (SHIFTED ? L::W[i] : 1.0);
+          if constexpr (c != 0.0) acc += Real(c) * q[i];
+        });
+        if constexpr (SHIFTED)
+          m[k][l] = acc * P.inv_s + P.rho0 * Real(weight_moment<L>(k, l));
+        else
+          m[k][l] = acc;
+      }
+    });
+  });
+
+  Real rho = m[0][0];
+  Real ux, uy, e = Real(0);
+  if constexpr (THERMAL) {
+    // FP64 recovery of rho, u and theta from the energy moment 2 rho E = sum f xi^2 (Sec. II.A)
+    double r = 0.0, jx = 0.0, jy = 0.0, e2 = 0.0;
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      double fi;
+      constexpr double wi = L::W[i];
+      if constexpr (SHIFTED)
+        fi = wi * ((double)P.rho0 + (double)q[i] * (double)P.inv_s);
+      else
+        fi = (double)q[i];
+      constexpr double cx = L::CX[i], cy = L::CY[i], c_sq = cx * cx + cy * cy;
+      r += fi;
+      if constexpr (cx != 0.0) jx += cx * fi;
+      if constexpr (cy != 0.0) jy += cy * fi;
+      if constexpr (c_sq != 0.0) e2 += c_sq * fi;
+    });
+    const double uxd = jx / r, uyd = jy / r;
+    const double theta = (e2 / r - uxd * uxd - uyd * uyd) / (2.0 * c2);
+    rho = (Real)r;
+    ux = (Real)uxd;
+    uy = (Real)uyd;
+    e = (Real)(c2 * (theta - 1.0));
+  } else {
+    const Real irho = Real(1) / rho;
+    ux = m[1][0] * irho;
+    uy = m[0][1] * irho;
+  }
+
+  Real A[5][5];
+  equilibrium_coefficients<L, THERMAL>(rho, ux, uy, e, A);
+
+  // Hermite moments of f: M[a][b] = sum_{k<=a, l<=b} he_coef(a,k) he_coef(b,l) m[k][l]
+  auto hmom = [&](auto Aa, auto Bb) -> Real {
+    constexpr int a = LBM_CI(Aa);
+    constexpr int b = LBM_CI(Bb);
+    Real acc = Real(0);
+    sfor<0, a + 1>([&](auto K) {
+      constexpr int k = LBM_CI(K);
+      sfor<0, b + 1>([&](auto Lq) {
+        constexpr int l = LBM_CI(Lq);
+        constexpr double h = he_coef(a, k, c2) * he_coef(b, l, c2);
+        if constexpr (h != 0.0) acc += Real(h) * m[k][l];
+      });
+    });
+    return acc;
+  };
+
+  Real B[5][5];
+  if constexpr (COLL == COLL_PR) {
+    // a1^(n) = sum_i H^(n)_i (f_i - f_i^(0)), n = 2..N (Sec. II.E); by orthogonality of the kept
+    // basis, sum_i H_i f_i^(0) = a0 on the orders f^(0) carries and 0 above them.
+    sfor<2, L::NMAX + 1>([&](auto N) {
+      constexpr int n = LBM_CI(N);
+      sfor<0, n + 1>([&](auto Aa) {
+        constexpr int a = LBM_CI(Aa);
+        constexpr int b = n - a;
+        if constexpr (L::keep(a, b)) {
+          Real v = hmom(IC<a>{}, IC<b>{});
+          if (n <= P.neq) v -= A[a][b];
+          B[a][b] = v;
+        }
+      });
+    });
+  } else if constexpr (COLL == COLL_RR) {
+    B[2][0] = hmom(IC<2>{}, IC<0>{}) - A[2][0];
+    B[1][1] = hmom(IC<1>{}, IC<1>{}) - A[1][1];
+    B[0][2] = hmom(IC<0>{}, IC<2>{}) - A[0][2];
+    a1_third_from_second<L, THERMAL>(ux, uy, B);
+    if constexpr (THERMAL && L::NMAX >= 3) {
+      // App. C steps 2-4: projected a1^(3), averaged temperature-gradient terms, rebuilt a1^(3)
+      const bool eq3 = 3 <= P.neq;
+      const Real p30 = hmom(IC<3>{}, IC<0>{}) - (eq3 ? A[3][0] : Real(0));
+      const Real p21 = hmom(IC<2>{}, IC<1>{}) - (eq3 ? A[2][1] : Real(0));
+      const Real p12 = hmom(IC<1>{}, IC<2>{}) - (eq3 ? A[1][2] : Real(0));
+      const Real p03 = hmom(IC<0>{}, IC<3>{}) - (eq3 ? A[0][3] : Real(0));
+      const Real third = Real(1) / Real(3);
+      const Real gx = Real(0.5) * ((ux * B[2][0] - p30 * third) + (Real(2) * uy * B[1][1] + ux * B[0][2] - p12));
+      const Real gy = Real(0.5) * ((uy * B[0][2] - p03 * third) + (Real(2) * ux * B[1][1] + uy * B[2][0] - p21));
+      B[3][0] -= Real(3) * gx;
+      B[2][1] -= gy;
+      B[1][2] -= gx;
+      B[0][3] -= Real(3) * gy;
+    }
+    a1_fourth<L, THERMAL>(ux, uy, e, B);
+  }
+
+  // --- coefficients of the rebuilt populations (Eq. GenRegCollision) ---
+  Real C[5][5];
+  sfor<0, L::NMAX + 1>([&](auto N) {
+    constexpr int n = LBM_CI(N);
+    sfor<0, n + 1>([&](auto Aa) {
+      constexpr int a = LBM_CI(Aa);
+      constexpr int b = n - a;
+      if constexpr (L::keep(a, b)) {
+        constexpr double sc = 1.0 / (factorial(a) * factorial(b) * ipow(c2, a + b));
+        Real v = (n <= P.neq) ? A[a][b] : Real(0);
+        if constexpr (COLL == COLL_BGK) {
+          v *= P.omega;
+        } else if constexpr (n >= 2) {
+          if (n <= P.nreg) v += P.om1 * B[a][b];
+        }
+        if constexpr (SHIFTED) v *= P.s;
+        C[a][b] = v * Real(sc);
+      }
+    });
+  });
+
+  if constexpr (COLL == COLL_BGK) {
+    // f* = (1 - 1/tau) f + f^(0) / tau  (Sec. III.A)
+    const Real shift = SHIFTED ? -P.s * P.rho0 * P.omega : Real(0);
+    rebuild<L, SHIFTED>(C, [&](auto I, Real acc) {
+      constexpr int i = LBM_CI(I);
+      q[i] = P.om1 * q[i] + acc + shift;
+    });
+  } else {
+    // f* = f^(0) + (1 - 1/tau) f^(1)  (Eq. RegularizedCollision)
+    const Real shift = SHIFTED ? -P.s * P.rho0 : Real(0);
+    rebuild<L, SHIFTED>(C, [&](auto I, Real acc) {
+      constexpr int i = LBM_CI(I);
+      q[i] = acc + shift;
+    });
+  }
+}
+
+}  // namespace lbm

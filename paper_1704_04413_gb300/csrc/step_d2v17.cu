@@ -1,0 +1,7 @@
+// Stream-and-collide kernels of the D2V17 lattice (isothermal).
+#include "step.cuh"
+
+cudaError_t lbm_launch_step_d2v17(int coll, int prec, const void* fin, void* fout, const lbm::StepGeom& g,
+                                 const lbm::CollParamsD& pd, cudaStream_t st) {
+  return lbm::launch_step_lattice<lbm::D2V17, false>(coll, prec, fin, fout, g, pd, st);
+}

@@ -1,0 +1,205 @@
+"""Thin ctypes binding of liblbm (include/lbm.h): same names, argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  Arrays may be numpy
+float64 arrays (host) or CUDA torch tensors of dtype float64 (device; passed by
+data_ptr with on_device=1).  Importing this module loads the in-tree
+liblbm.so and raises if it is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+D2Q9, D2V17, D2V37 = 0, 1, 2
+BGK, PR, RR = 0, 1, 2
+PERIODIC, ZERO_GRADIENT = 0, 1
+F64, F32, F16_SHIFT, BF16_SHIFT = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EIO = 0, -1, -2, -3, -4, -5, -6
+
+LATTICES = {"D2Q9": D2Q9, "D2V17": D2V17, "D2V37": D2V37}
+COLLISIONS = {"bgk": BGK, "pr": PR, "rr": RR}
+STORAGES = {"f64": F64, "f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT}
+EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_moments",
+            "lbm_conservation", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
+            "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error"]
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("hermite_order", ctypes.c_int), ("reg_order", ctypes.c_int),
+                ("collision", ctypes.c_int), ("thermal", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nu", ctypes.c_double), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("storage", ctypes.c_int), ("compute", ctypes.c_int), ("rho0", ctypes.c_double),
+                ("store_scale", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (msg, code, lbm_strerror(code)))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbm.so (raises OSError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError("liblbm.so not built at %s (run paper_1704_04413_gb300/build.py)" % path)
+    lib = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "lbm_lattice_info": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, dp, dp]),
+        "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.POINTER(vp)]),
+        "lbm_destroy": (None, [vp]),
+        "lbm_init": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, ctypes.c_int]),
+        "lbm_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_moments": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int]),
+        "lbm_conservation": (ctypes.c_int, [vp, dp]),
+        "lbm_diagnostics": (ctypes.c_int, [vp, dp]),
+        "lbm_get_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "lbm_set_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "lbm_step_count": (ctypes.c_longlong, [vp]),
+        "lbm_tau": (ctypes.c_double, [vp]),
+        "lbm_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "lbm_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbm_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _check(rc, ctx=None, what="liblbm"):
+    if rc != OK:
+        detail = load().lbm_last_error(ctx).decode() if ctx else ""
+        raise LbmError(rc, "%s: %s" % (what, detail) if detail else what)
+    return rc
+
+
+def lbm_strerror(code: int) -> str:
+    return load().lbm_strerror(code).decode()
+
+
+def lbm_last_error(ctx) -> str:
+    return load().lbm_last_error(ctx).decode()
+
+
+def lbm_lattice_info(lattice):
+    lat = LATTICES.get(lattice, lattice)
+    V = ctypes.c_int()
+    cx = (ctypes.c_int * 64)()
+    cy = (ctypes.c_int * 64)()
+    w = (ctypes.c_double * 64)()
+    cs2 = ctypes.c_double()
+    _check(load().lbm_lattice_info(lat, ctypes.byref(V), cx, cy, w, ctypes.byref(cs2)), what="lbm_lattice_info")
+    n = V.value
+    return n, np.array(cx[:n]), np.array(cy[:n]), np.array(w[:n]), cs2.value
+
+
+def make_params(lattice="D2Q9", nx=64, ny=64, tau=0.0, nu=0.0, collision="rr", hermite_order=2, reg_order=0,
+                thermal=False, bc_x=PERIODIC, bc_y=PERIODIC, storage="f32", rho0=0.0, store_scale=0.0,
+                stream=None) -> lbm_params:
+    st = STORAGES.get(storage, storage)
+    compute = F64 if st == F64 else F32
+    return lbm_params(LATTICES.get(lattice, lattice), hermite_order, reg_order,
+                      COLLISIONS.get(collision, collision), int(thermal), nx, ny, float(nu), float(tau), bc_x, bc_y,
+                      st, compute, float(rho0), float(store_scale), stream)
+
+
+def lbm_create(params: lbm_params):
+    ctx = ctypes.c_void_p()
+    _check(load().lbm_create(ctypes.byref(params), ctypes.byref(ctx)), what="lbm_create")
+    return ctx
+
+
+def lbm_destroy(ctx) -> None:
+    load().lbm_destroy(ctx)
+
+
+def lbm_init(ctx, rho, ux, uy, theta=None, grad_u=None):
+    ptrs = [_ptr(a) for a in (rho, ux, uy, theta, grad_u)]
+    flags = {p[1] for p in ptrs if p[1] is not None}
+    if len(flags) != 1:
+        raise TypeError("mix of host and device arrays")
+    return _check(load().lbm_init(ctx, *[p[0] for p in ptrs], flags.pop()), ctx, "lbm_init")
+
+
+def lbm_step(ctx, n: int = 1):
+    return _check(load().lbm_step(ctx, int(n)), ctx, "lbm_step")
+
+
+def lbm_moments(ctx, rho=None, ux=None, uy=None, theta=None):
+    ptrs = [_ptr(a) for a in (rho, ux, uy, theta)]
+    flags = {p[1] for p in ptrs if p[1] is not None}
+    if len(flags) != 1:
+        raise TypeError("mix of host and device arrays")
+    return _check(load().lbm_moments(ctx, *[p[0] for p in ptrs], flags.pop()), ctx, "lbm_moments")
+
+
+def lbm_conservation(ctx, raise_unstable=True) -> np.ndarray:
+    out = np.zeros(4)
+    rc = load().lbm_conservation(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != EUNSTABLE or raise_unstable:
+        _check(rc, ctx, "lbm_conservation")
+    return out
+
+
+def lbm_diagnostics(ctx, raise_unstable=True) -> np.ndarray:
+    out = np.zeros(4)
+    rc = load().lbm_diagnostics(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != EUNSTABLE or raise_unstable:
+        _check(rc, ctx, "lbm_diagnostics")
+    return out
+
+
+def lbm_get_populations(ctx, f):
+    p, dev = _ptr(f)
+    return _check(load().lbm_get_populations(ctx, p, dev), ctx, "lbm_get_populations")
+
+
+def lbm_set_populations(ctx, f):
+    p, dev = _ptr(f)
+    return _check(load().lbm_set_populations(ctx, p, dev), ctx, "lbm_set_populations")
+
+
+def lbm_step_count(ctx) -> int:
+    return load().lbm_step_count(ctx)
+
+
+def lbm_tau(ctx) -> float:
+    return load().lbm_tau(ctx)
+
+
+def lbm_save(ctx, path: str):
+    return _check(load().lbm_save(ctx, path.encode()), ctx, "lbm_save")
+
+
+def lbm_load(ctx, path: str):
+    return _check(load().lbm_load(ctx, path.encode()), ctx, "lbm_load")

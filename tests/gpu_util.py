@@ -1,0 +1,76 @@
+"""Helpers of the GPU tests: contexts on cuda:0 through the C ABI, the
+velocity-order permutation between the library and the oracle, and error norms."""
+import numpy as np
+
+from oracle import oracle as orc
+
+
+def lib():
+    from paper_1704_04413_gb300 import lbm
+    lbm.load()
+    return lbm
+
+
+def stream():
+    import torch
+    torch.cuda.set_device(0)
+    return torch.cuda.current_stream().cuda_stream
+
+
+def perm(name):
+    """Index array P with f_lib = f_oracle[P] (matched by velocity vector)."""
+    V, cx, cy, _, _ = lib().lbm_lattice_info(name)
+    L = orc.lattice(name)
+    idx = {(int(a), int(b)): k for k, (a, b) in enumerate(zip(L.cx, L.cy))}
+    return np.array([idx[(int(a), int(b))] for a, b in zip(cx, cy)])
+
+
+class Ctx:
+    """A library context; closes on exit."""
+
+    def __init__(self, name, nx, ny, tau, coll="rr", neq=2, nreg=0, storage="f32", thermal=False,
+                 bcx=0, bcy=0, rho0=0.0, scale=0.0):
+        m = lib()
+        self.m = m
+        self.name, self.nx, self.ny = name, nx, ny
+        self.V = m.lbm_lattice_info(name)[0]
+        self.P = perm(name)
+        p = m.make_params(name, nx, ny, tau=tau, collision=coll, hermite_order=neq, reg_order=nreg,
+                          thermal=thermal, bc_x=bcx, bc_y=bcy, storage=storage, rho0=rho0, store_scale=scale,
+                          stream=stream())
+        self.ctx = m.lbm_create(p)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.m.lbm_destroy(self.ctx)
+
+    def set_oracle_f(self, f_orc):
+        self.m.lbm_set_populations(self.ctx, np.ascontiguousarray(f_orc[self.P]))
+
+    def get_oracle_f(self):
+        g = np.empty((self.V, self.ny, self.nx))
+        self.m.lbm_get_populations(self.ctx, g)
+        out = np.empty_like(g)
+        out[self.P] = g
+        return out
+
+    def init(self, fl, theta=None, grad=True):
+        self.m.lbm_init(self.ctx, fl.rho, fl.ux, fl.uy, theta, fl.grad_u if grad else None)
+
+    def step(self, n=1):
+        self.m.lbm_step(self.ctx, n)
+
+    def moments(self):
+        a = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        self.m.lbm_moments(self.ctx, *a)
+        return a
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))

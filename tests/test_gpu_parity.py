@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: FP32 compute and storage within 1e-6 relative per population for
+one collision and within 1e-4 relative L2 on rho and u after 500 steps of the
+64x64 shear layer; FP64 compute and storage within 1e-12 (per collision) and
+1e-10 relative L2 after 500 steps.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1704_04413_gb300 import workloads as wl
+
+from gpu_util import Ctx, lib, max_rel, perm, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_COLL = {"f32": 1e-6, "f64": 1e-12}
+
+# (lattice, collision, hermite_order, reg_order, thermal)
+MODES = [
+    ("D2Q9", "bgk", 2, 0, False), ("D2Q9", "pr", 2, 2, False), ("D2Q9", "pr", 4, 4, False),
+    ("D2Q9", "rr", 2, 0, False), ("D2Q9", "rr", 4, 0, False), ("D2Q9", "rr", 2, 3, False),
+    ("D2V17", "bgk", 3, 0, False), ("D2V17", "pr", 3, 0, False), ("D2V17", "rr", 3, 0, False),
+    ("D2V17", "rr", 2, 2, False),
+    ("D2V37", "bgk", 4, 0, False), ("D2V37", "pr", 4, 0, False), ("D2V37", "rr", 4, 0, False),
+    ("D2V37", "rr", 2, 3, False), ("D2V37", "pr", 3, 4, False),
+    ("D2V37", "bgk", 4, 0, True), ("D2V37", "pr", 4, 0, True), ("D2V37", "rr", 4, 0, True),
+    ("D2V37", "rr", 3, 4, True),
+]
+
+
+def oracle_state(name, nx, ny, seed, thermal, eps=0.02, neq=None):
+    """Oracle-initialised non-equilibrium populations: f^(0) of smooth random fields times (1 + eta)."""
+    L = orc.lattice(name)
+    fl = wl.random_fields(nx, ny, seed, u_scale=0.08, theta_amp=0.08 if thermal else 0.0)
+    op = orc.params(name, nx, ny, 0.7, "bgk", neq or L.nmax, thermal=thermal)
+    f = orc.init(op, fl.rho, fl.ux, fl.uy, fl.theta, None)
+    return f * (1.0 + wl.population_noise(L.V, nx, ny, seed + 1, eps))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("name,coll,neq,nreg,thermal", MODES)
+def test_one_step_matches_oracle(name, coll, neq, nreg, thermal, storage):
+    nx, ny, tau = 300, 5, 0.62  # 300 = two 128-wide tiles and a ragged tail
+    f = oracle_state(name, nx, ny, 11, thermal)
+    op = orc.params(name, nx, ny, tau, coll, neq, nreg, thermal=thermal)
+    ref = orc.step(op, f)
+    with Ctx(name, nx, ny, tau, coll, neq, nreg, storage, thermal) as c:
+        c.set_oracle_f(f)
+        c.step(1)
+        got = c.get_oracle_f()
+    assert max_rel(got, ref) <= TOL_COLL[storage]
+
+
+@pytest.mark.parametrize("bcx,bcy", [(1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("name,thermal", [("D2Q9", False), ("D2V17", False), ("D2V37", True)])
+def test_zero_gradient_boundaries_match_oracle(name, thermal, bcx, bcy):
+    nx, ny, tau = 133, 9, 0.7
+    f = oracle_state(name, nx, ny, 3, thermal)
+    op = orc.params(name, nx, ny, tau, "rr", orc.lattice(name).nmax, thermal=thermal, bc_x=bcx, bc_y=bcy)
+    ref = orc.step(op, f, 3)
+    with Ctx(name, nx, ny, tau, "rr", orc.lattice(name).nmax, 0, "f64", thermal, bcx, bcy) as c:
+        c.set_oracle_f(f)
+        c.step(3)
+        got = c.get_oracle_f()
+    assert max_rel(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 3), (5, 7), (1, 40), (129, 1)])
+@pytest.mark.parametrize("name", ["D2Q9", "D2V37"])
+def test_degenerate_and_tiny_grids(name, nx, ny):
+    """Grids narrower than the stencil (periodic images wrap several times) and single rows/columns."""
+    f = oracle_state(name, nx, ny, 5, False)
+    op = orc.params(name, nx, ny, 0.8, "rr", orc.lattice(name).nmax)
+    ref = orc.step(op, f, 2)
+    with Ctx(name, nx, ny, 0.8, "rr", orc.lattice(name).nmax, 0, "f64") as c:
+        c.set_oracle_f(f)
+        c.step(2)
+        got = c.get_oracle_f()
+    assert max_rel(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("name,neq,thermal", [("D2Q9", 2, False), ("D2Q9", 4, False), ("D2V17", 3, False),
+                                              ("D2V37", 4, False), ("D2V37", 4, True)])
+def test_init_and_moments_match_oracle(name, neq, thermal, storage):
+    nx, ny, tau = 70, 33, 0.66
+    fl = wl.random_fields(nx, ny, 21, theta_amp=0.1 if thermal else 0.0)
+    grad = np.random.default_rng(1).normal(size=(4, ny, nx)) * 1e-3
+    fl.grad_u = grad
+    op = orc.params(name, nx, ny, tau, "rr", neq, thermal=thermal)
+    ref = orc.init(op, fl.rho, fl.ux, fl.uy, fl.theta, grad)
+    mref = orc.moments(op, ref)
+    with Ctx(name, nx, ny, tau, "rr", neq, 0, storage, thermal) as c:
+        c.init(fl, fl.theta)
+        got = c.get_oracle_f()
+        mom = c.moments()
+        cons = c.m.lbm_conservation(c.ctx)
+    tol = TOL_COLL[storage]
+    assert max_rel(got, ref) <= tol
+    for a, b in zip(mom, mref):
+        assert np.max(np.abs(a - b)) <= 10 * tol * max(1.0, np.max(np.abs(b)))
+    cref = orc.conservation(op, ref)
+    assert np.max(np.abs(cons - cref)) <= 10 * tol * np.abs(cref).max()
+
+
+@pytest.mark.parametrize("coll,nreg", [("bgk", 0), ("pr", 2), ("rr", 0)])
+def test_shear_layer_500_steps(coll, nreg):
+    """64x64 doubly periodic shear layer, Re = 1e4, Ma = 0.1, 2nd-order equilibrium, 500 steps."""
+    L, name = 64, "D2Q9"
+    Lt = orc.lattice(name)
+    u0, nu, _ = wl.shear_layer_params(L, np.sqrt(Lt.cs2), 0.1, 1e4)
+    fl = wl.double_shear_layer(L, u0)
+    tau = orc.tau_from_nu(Lt.cs2, nu)
+    op = orc.params(name, L, L, tau, coll, 2, nreg)
+    f = orc.step(op, orc.init(op, fl.rho, fl.ux, fl.uy, None, fl.grad_u), 500)
+    r_o, ux_o, uy_o, _ = orc.moments(op, f)
+    cons_o = orc.conservation(op, f)
+    for storage, tol in (("f32", 1e-4), ("f64", 1e-10)):
+        with Ctx(name, L, L, tau, coll, 2, nreg, storage) as c:
+            c.init(fl)
+            c.step(500)
+            r, ux, uy, _ = c.moments()
+            cons = c.m.lbm_conservation(c.ctx)
+        assert rel_l2(r, r_o) <= tol
+        assert rel_l2(np.stack([ux, uy]), np.stack([ux_o, uy_o])) <= tol
+        assert abs(cons[0] - cons_o[0]) <= tol * abs(cons_o[0])
+
+
+def test_diagnostics_match_oracle():
+    L, name = 64, "D2Q9"
+    Lt = orc.lattice(name)
+    u0, nu, _ = wl.shear_layer_params(L, np.sqrt(Lt.cs2), 0.1, 1e4)
+    fl = wl.double_shear_layer(L, u0)
+    tau = orc.tau_from_nu(Lt.cs2, nu)
+    op = orc.params(name, L, L, tau, "rr", 2)
+    f = orc.step(op, orc.init(op, fl.rho, fl.ux, fl.uy, None, fl.grad_u), 50)
+    d_o = orc.diagnostics(*orc.moments(op, f)[:3])
+    with Ctx(name, L, L, tau, "rr", 2, 0, "f64") as c:
+        c.init(fl)
+        c.step(50)
+        d = c.m.lbm_diagnostics(c.ctx)
+    assert np.max(np.abs(d - d_o) / np.abs(d_o)) <= 1e-9
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("name,thermal", [("D2Q9", False), ("D2V17", False), ("D2V37", False), ("D2V37", True)])
+def test_shifted_low_precision_storage(name, thermal, storage, tol):
+    """Shifted FP16/BF16 storage g = (f/w - rho0) s: one step against the oracle, error relative to
+    the deviation scale max|f/w - rho0| (what the format resolves)."""
+    nx, ny, tau = 150, 6, 0.7
+    f = oracle_state(name, nx, ny, 8, thermal)
+    Lt = orc.lattice(name)
+    op = orc.params(name, nx, ny, tau, "rr", Lt.nmax, thermal=thermal)
+    ref = orc.step(op, f)
+    with Ctx(name, nx, ny, tau, "rr", Lt.nmax, 0, storage, thermal) as c:
+        c.set_oracle_f(f)
+        c.step(1)
+        got = c.get_oracle_f()
+    w = Lt.w[:, None, None]
+    dev = np.abs(ref / w - 1.0).max()
+    assert np.max(np.abs(got - ref) / w) <= tol * dev
+
+
+def test_checkpoint_round_trip_is_bitwise():
+    name, nx, ny = "D2V17", 96, 40
+    Lt = orc.lattice(name)
+    u0, nu, _ = wl.shear_layer_params(nx, np.sqrt(Lt.cs2), 0.1, 3e4)
+    fl = wl.double_shear_layer(nx, u0, ny=ny)
+    with Ctx(name, nx, ny, 0.6, "rr", 3, 0, "f32") as a, Ctx(name, nx, ny, 0.6, "rr", 3, 0, "f32") as b:
+        a.init(fl)
+        a.step(20)
+        path = os.path.join(tempfile.mkdtemp(), "ck.bin")
+        a.m.lbm_save(a.ctx, path)
+        a.step(20)
+        b.m.lbm_load(b.ctx, path)
+        assert b.m.lbm_step_count(b.ctx) == 20
+        b.step(20)
+        fa, fb = a.get_oracle_f(), b.get_oracle_f()
+    assert np.array_equal(fa, fb)
+
+
+def test_checkpoint_rejects_other_parameters():
+    name, nx, ny = "D2Q9", 32, 32
+    m = lib()
+    with Ctx(name, nx, ny, 0.6, "rr", 2) as a, Ctx(name, nx, ny, 0.7, "rr", 2) as b:
+        fl = wl.random_fields(nx, ny, 1)
+        fl.grad_u = None
+        a.init(fl, grad=False)
+        path = os.path.join(tempfile.mkdtemp(), "ck.bin")
+        m.lbm_save(a.ctx, path)
+        with pytest.raises(m.LbmError) as e:
+            m.lbm_load(b.ctx, path)
+        assert e.value.code == m.EINVAL
+
+
+def test_nonfinite_state_is_reported():
+    """Host-side fault injection: a NaN population makes the conservation sums report LBM_EUNSTABLE."""
+    name, nx, ny = "D2Q9", 40, 8
+    m = lib()
+    f = oracle_state(name, nx, ny, 2, False)
+    f[3, 4, 5] = np.nan
+    with Ctx(name, nx, ny, 0.7) as c:
+        c.set_oracle_f(f)
+        c.step(2)
+        with pytest.raises(m.LbmError) as e:
+            m.lbm_conservation(c.ctx)
+        assert e.value.code == m.EUNSTABLE
+
+
+def test_mass_and_momentum_conserved_over_steps():
+    name, L = "D2V37", 128
+    Lt = orc.lattice(name)
+    u0, nu, _ = wl.shear_layer_params(L, np.sqrt(Lt.cs2), 0.1, 3e4)
+    fl = wl.double_shear_layer(L, u0)
+    with Ctx(name, L, L, orc.tau_from_nu(Lt.cs2, nu), "rr", 4, 0, "f64") as c:
+        c.init(fl)
+        c0 = c.m.lbm_conservation(c.ctx)
+        c.step(200)
+        c1 = c.m.lbm_conservation(c.ctx)
+    assert abs(c1[0] - c0[0]) <= 1e-12 * abs(c0[0])
+    assert np.max(np.abs(c1[1:3] - c0[1:3])) <= 1e-12 * abs(c0[0])
+
+
+def test_full_size_sampled_parity_d2v37():
+    """1024x1024 D2V37 RR FP32, the benchmark's largest shear-layer grid and launch shape: one step from the
+    oracle's initial state (f^(0) + f^(1)), 2000 sampled cells (including edges and corners) checked
+    cell by cell against the oracle."""
+    name, L = "D2V37", 1024
+    Lt = orc.lattice(name)
+    u0, nu, _ = wl.shear_layer_params(L, np.sqrt(Lt.cs2), 0.1, 3e4)
+    fl = wl.double_shear_layer(L, u0)
+    tau = orc.tau_from_nu(Lt.cs2, nu)
+    op = orc.params(name, L, L, tau, "rr", 4)
+    f = orc.init(op, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([rng.integers(0, L * L, 1900), np.arange(0, L, 11), np.arange(0, L * L, L * 37)[:30],
+                            [L - 1, L * L - 1, L * (L - 1)]])
+    with Ctx(name, L, L, tau, "rr", 4, 0, "f32") as c:
+        c.set_oracle_f(f)
+        c.step(1)
+        got = c.get_oracle_f()
+    ref = orc.step_cells(op, f, cells)
+    got_s = got.reshape(Lt.V, -1)[:, cells].T
+    assert max_rel(got_s, ref) <= 1e-6
