@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the RR stream-and-collide step on GB300 (one JSON line on stdout).
+
+Workload: the doubly periodic shear layer of Sec. III.B at Re = 3e4, Ma = 0.1,
+on 1024^2 grids, one context per lattice: D2Q9 (2nd-order equilibrium),
+D2V17 (3rd order) and D2V37 (4th order), RR collision, FP32 compute and FP32
+storage.  One bench step = one lbm_step on each of the three lattices.
+`value` is the aggregate GLUPS (cells updated per second, all lattices, all
+ranks); per-lattice GLUPS, HBM roofline fractions and the low-precision
+(shifted FP16 / BF16) and FP64 variants are reported alongside.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the method written plainly in C)
+on the host cores for the same workload, on a bounded band of rows.
+Under torchrun each rank runs the full workload on its own GPU (weak scaling,
+no collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import signal
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1704_04413_gb300 import workloads as wl  # noqa: E402
+
+GRID = 1024
+RE, MACH = 3e4, 0.1
+LATTICES = (("D2Q9", 2), ("D2V17", 3), ("D2V37", 4))
+BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+METRIC = "RR stream-collide GLUPS & HBM-roofline fraction per lattice; low-prec vs FP32"
+REF_BAND = 128  # rows of the oracle's sample band
+PROFILE = os.path.join(ROOT, "profiles", "step_d2v37_rr_f32_1024.txt")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1704_04413_gb300", "csrc")
+    for fn in ("lattice.cuh", "collide.cuh", "step.cuh", "step_d2v37.cu"):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """dram bytes per launch of the D2V37 RR FP32 kernel from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    for line in open(PROFILE):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = "/tmp/lbm_clocks_%d_%d.csv" % (os.getpid(), index)
+        self.proc = None
+        self.index = index
+        self.window = None
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def __enter__(self):
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.send_signal(signal.SIGTERM)
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        if self.window:  # keep the samples taken inside the timed region (host wall clock, 0.1 s slack)
+            import datetime
+            def ts(r):
+                try:
+                    return datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    return None
+            inside = [r for r in rows if ts(r) is not None and self.window[0] - 0.1 <= ts(r) <= self.window[1] + 0.1]
+            rows = inside or rows[-1:]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def shear_fields(name, L):
+    from paper_1704_04413_gb300 import lbm
+    V, cx, cy, w, cs2 = lbm.lbm_lattice_info(name)
+    u0, nu, _ = wl.shear_layer_params(L, np.sqrt(cs2), MACH, RE)
+    return V, cs2, nu, wl.double_shear_layer(L, u0)
+
+
+def make_contexts(storage, stream):
+    from paper_1704_04413_gb300 import lbm
+    ctxs = []
+    for name, neq in LATTICES:
+        V, cs2, nu, fl = shear_fields(name, GRID)
+        p = lbm.make_params(name, GRID, GRID, nu=nu, collision="rr", hermite_order=neq, storage=storage,
+                            stream=stream)
+        ctx = lbm.lbm_create(p)
+        lbm.lbm_init(ctx, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+        ctxs.append((name, V, ctx, fl))
+    return ctxs
+
+
+def timed_steps(ctxs, steps, warmup, stream_t):
+    """Per-lattice kernel ms (events around each launch) and the whole-region ms."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    for _ in range(warmup):
+        for _, _, ctx, _ in ctxs:
+            lbm.lbm_step(ctx, 1)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+          for _ in ctxs]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.time()
+    t0.record(stream_t)
+    for k in range(steps):
+        for j, (_, _, ctx, _) in enumerate(ctxs):
+            ev[j][k][0].record(stream_t)
+            lbm.lbm_step(ctx, 1)
+            ev[j][k][1].record(stream_t)
+    t1.record(stream_t)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    per = [float(np.mean([a.elapsed_time(b) for a, b in ev[j]])) for j in range(len(ctxs))]
+    return per, t0.elapsed_time(t1), (w0, w1)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    lbm.load()
+    torch.cuda.set_device(local_rank)
+    stream_t = torch.cuda.Stream()
+    torch.cuda.set_stream(stream_t)
+    st = stream_t.cuda_stream
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    ncell = GRID * GRID
+
+    # ---- headline: FP32 compute + storage, RR, three lattices ----
+    ctxs = make_contexts("f32", st)
+    if world > 1:
+        torch.distributed.barrier()
+    with Clocks(local_rank) as clk:
+        per, total_ms, window = timed_steps(ctxs, args.steps, args.warmup, stream_t)
+        clk.mark(*window)
+    if world > 1:
+        torch.distributed.barrier()
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = len(ctxs) * ncell * args.steps * world / (total_ms * 1e-3) / 1e9
+    per_lattice = {}
+    for (name, V, ctx, _), ms in zip(ctxs, per):
+        glups = ncell / (ms * 1e-3) / 1e9
+        gbs = glups * 2 * V * BYTES["f32"]
+        per_lattice[name] = {"f32": {"glups": round(glups, 3), "ms": round(ms, 5), "gbs": round(gbs, 1),
+                                     "frac": round(gbs / hbm_peak, 4)}}
+    # dominant kernel: D2V37 RR FP32
+    dom_ms = per[-1]
+    dom_bytes = 2 * 37 * BYTES["f32"] * ncell
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                "kernel": "k_step<D2V37,RR,isothermal,f32,f32> 1024^2", "algorithmic_bytes": dom_bytes,
+                "peak_source": peak_src + " hbm_gbs (copy)"}
+    # ---- e2e through the C ABI with host buffers (pinned), every step: init from host, step, moments to host ----
+    h2d = d2h = 0
+    hosts = []
+    for name, V, ctx, fl in ctxs:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hosts.append((ctx, pin(fl.rho), pin(fl.ux), pin(fl.uy), pin(fl.grad_u),
+                      [torch.empty((GRID, GRID), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]))
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    for _ in range(e2e_steps):
+        for ctx, r, u, v, g, outs in hosts:
+            lbm.lbm_init(ctx, r, u, v, None, g)
+            lbm.lbm_step(ctx, 1)
+            lbm.lbm_moments(ctx, outs[0], outs[1], outs[2])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t_e
+    for _, r, u, v, g, outs in hosts:
+        h2d += r.nbytes + u.nbytes + v.nbytes + g.nbytes
+        d2h += sum(o.nbytes for o in outs)
+    e2e = {"value": round(len(ctxs) * ncell * e2e_steps / e2e_s / 1e9, 4), "unit": "GLUPS",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "path": "lbm_init(host rho,u,grad_u) + lbm_step(1) + lbm_moments(host) per lattice per step"}
+    for _, _, ctx, _ in ctxs:
+        lbm.lbm_destroy(ctx)
+
+    # ---- low precision (shifted FP16 / BF16 storage) and FP64, same workload ----
+    for storage, k in (("f16", args.steps), ("bf16", args.steps), ("f64", max(2, min(args.steps // 10, 50)))):
+        cs = make_contexts(storage, st)
+        per_s, _, _ = timed_steps(cs, k, min(args.warmup, 2), stream_t)
+        for (name, V, ctx, _), ms in zip(cs, per_s):
+            glups = ncell / (ms * 1e-3) / 1e9
+            gbs = glups * 2 * V * BYTES[storage]
+            per_lattice[name][storage] = {"glups": round(glups, 3), "ms": round(ms, 5), "gbs": round(gbs, 1),
+                                          "frac": round(gbs / hbm_peak, 4),
+                                          "vs_f32": round(glups / per_lattice[name]["f32"]["glups"], 3)}
+            lbm.lbm_destroy(ctx)
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "double shear layer Re=3e4 Ma=0.1 (kappa=80, delta=0.05), 1024x1024 periodic; "
+                                   "one step = lbm_step on D2Q9 (N=2), D2V17 (N=3), D2V37 (N=4), RR, FP32",
+                       "grid": GRID, "lattices": [n for n, _ in LATTICES], "collision": "rr",
+                       "storage": "f32", "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
+                             "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
+            "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
+            "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(min_seconds=10.0)
+        print(json.dumps(line), flush=True)
+
+
+def oracle_sample_step(pairs):
+    from oracle import oracle as orc
+    for p, f in pairs:
+        f[0] = orc.step(p, f[0])
+
+
+def oracle_setup(band):
+    from oracle import oracle as orc
+    pairs = []
+    for name, neq in LATTICES:
+        L = orc.lattice(name)
+        u0, nu, _ = wl.shear_layer_params(GRID, np.sqrt(L.cs2), MACH, RE)
+        fl = wl.double_shear_layer(GRID, u0)
+        rows = slice(GRID // 4 - band // 2, GRID // 4 + band // 2)  # band across the lower shear layer
+        p = orc.params(name, GRID, band, orc.tau_from_nu(L.cs2, nu), "rr", neq)
+        f = orc.init(p, fl.rho[rows].copy(), fl.ux[rows].copy(), fl.uy[rows].copy(), None,
+                     fl.grad_u[:, rows].copy())
+        pairs.append((p, [f]))
+    return pairs
+
+
+def cpu_baseline(min_seconds=10.0, max_steps=20):
+    from oracle import oracle as orc
+    orc.build_oracle()
+    pairs = oracle_setup(REF_BAND)
+    oracle_sample_step(pairs)  # warm-up
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps and (time.perf_counter() - t0) < min_seconds:
+        oracle_sample_step(pairs)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(len(pairs) * GRID * REF_BAND * n / dt / 1e9, 6), "unit": "GLUPS",
+            "cores": orc.num_threads(), "kind": "oracle",
+            "sample": "%d steps of a %dx%d periodic band across the lower shear layer, per lattice "
+                      "(D2Q9, D2V17, D2V37 RR), FP64 C oracle with OpenMP over rows" % (n, GRID, REF_BAND)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    orc.build_oracle()
+    pairs = oracle_setup(REF_BAND)
+    for _ in range(args.warmup):
+        oracle_sample_step(pairs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample_step(pairs)
+    dt = time.perf_counter() - t0
+    value = len(pairs) * GRID * REF_BAND * args.steps / dt / 1e9
+    sample = ("%dx%d periodic band across the lower shear layer per lattice (D2Q9 N=2, D2V17 N=3, D2V37 N=4, "
+              "RR), FP64 C oracle with OpenMP over rows" % (GRID, REF_BAND))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "double shear layer Re=3e4 Ma=0.1, 1024-wide grid; one step = one step of "
+                                   "each of D2Q9/D2V17/D2V37 RR (oracle on a band of rows)", "grid": GRID,
+                       "band_rows": REF_BAND},
+            "cpu_baseline": {"value": round(value, 6), "unit": "GLUPS", "cores": orc.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def kernel_only(args):
+    """One lattice, one storage format: warm-up then timed steps; prints per-step ms (profiling case)."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    torch.cuda.set_device(0)
+    stream_t = torch.cuda.Stream()
+    neq = dict(LATTICES)[args.kernel_only]
+    V, cs2, nu, fl = shear_fields(args.kernel_only, args.grid)
+    p = lbm.make_params(args.kernel_only, args.grid, args.grid, nu=nu, collision="rr", hermite_order=neq,
+                        storage=args.storage, stream=stream_t.cuda_stream)
+    ctx = lbm.lbm_create(p)
+    lbm.lbm_init(ctx, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+    per, total, _ = timed_steps([(args.kernel_only, V, ctx, fl)], args.steps, args.warmup, stream_t)
+    glups = args.grid * args.grid / (per[0] * 1e-3) / 1e9
+    print(json.dumps({"kernel_only": args.kernel_only, "grid": args.grid, "storage": args.storage,
+                      "ms": per[0], "glups": glups, "gbs": glups * 2 * V * BYTES[args.storage]}))
+    lbm.lbm_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kernel-only", default=None, metavar="LATTICE",
+                    help="profiling case: run only this lattice's RR step (for ncu captures)")
+    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--storage", default="f32")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if args.kernel_only:
+        kernel_only(args)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -171,6 +171,29 @@ __device__ __forceinline__ void rebuild(const Real (&C)[5][5], F&& emit) {
 }
 
 // ---------------------------------------------------------------------------
+// Reference state.  Moments are accumulated from the deviations
+// d_i = f_i - w_i rho_ref of the populations from the rest equilibrium
+// w_i rho_ref, whose Hermite moments are rho_ref for H^(0) and 0 for every
+// other kept tensor (orthogonality, App. D).  So
+//   M[a][b] = rho_ref [a=b=0] + kappa[a][b] + sum_i He(a,cx_i) He(b,cy_i) d_i,
+// with no large constant left to cancel in a1 = M - a0.  For plain storage
+// the reference is the rounded weight w^_i of the storage type (d_i = f_i - w^_i
+// is then exact whenever f_i is within a factor 2 of w_i) and
+// kappa[a][b] = sum_i He He (w^_i - w_i) restores the exact moments; shifted
+// storage already holds s (f_i/w_i - rho0) and has kappa = 0.
+// ---------------------------------------------------------------------------
+template <class L, class Real>
+__host__ __device__ constexpr double ref_weight(int i) {
+  return (double)(Real)L::W[i];
+}
+template <class L, class Real>
+__host__ __device__ constexpr double kappa(int a, int b) {
+  double s = 0.0;
+  for (int i = 0; i < L::Q; ++i) s += he(a, L::CX[i], L::CS2) * he(b, L::CY[i], L::CS2) * (ref_weight<L, Real>(i) - L::W[i]);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
 // One collision.  q holds the pulled populations in storage representation
 // (converted to Real) and receives the post-collision ones.
 // ---------------------------------------------------------------------------
@@ -179,9 +202,20 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
   constexpr double c2 = L::CS2;
   // highest monomial order of f the mode needs
   constexpr int PM = (COLL == COLL_PR) ? L::NMAX : (COLL == COLL_RR ? (THERMAL ? 3 : 2) : 1);
+  const Real rho_ref = SHIFTED ? P.rho0 : Real(1);
 
-  // --- monomial moments m[k][l] = sum_i f_i cx^k cy^l (Sec. II.A) ---
-  Real m[5][5];
+  // deviations from the reference (plain storage); shifted storage holds them already
+  Real d[L::Q];
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    if constexpr (SHIFTED)
+      d[i] = q[i];
+    else
+      d[i] = q[i] - Real(ref_weight<L, Real>(i));
+  });
+
+  // --- monomial moments of the deviations D[k][l] = sum_i d_i cx^k cy^l (Sec. II.A) ---
+  Real D[5][5];
   sfor<0, 5>([&](auto K) {
     constexpr int k = LBM_CI(K);
     sfor<0, 5 - k>([&](auto Lq) {
@@ -191,17 +225,35 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
         sfor<0, L::Q>([&](auto I) {
           constexpr int i = LBM_CI(I);
           constexpr double c = ipow(L::CX[i], k) * ipow(L::CY[i], l) * (SHIFTED ? L::W[i] : 1.0);
-          if constexpr (c != 0.0) acc += Real(c) * q[i];
+          if constexpr (c != 0.0) acc += Real(c) * d[i];
         });
-        if constexpr (SHIFTED)
-          m[k][l] = acc * P.inv_s + P.rho0 * Real(weight_moment<L>(k, l));
-        else
-          m[k][l] = acc;
+        D[k][l] = SHIFTED ? acc * P.inv_s : acc;
       }
     });
   });
 
-  Real rho = m[0][0];
+  // Hermite moments of f (see above)
+  auto hmom = [&](auto Aa, auto Bb) -> Real {
+    constexpr int a = LBM_CI(Aa);
+    constexpr int b = LBM_CI(Bb);
+    Real acc = Real(0);
+    sfor<0, a + 1>([&](auto K) {
+      constexpr int k = LBM_CI(K);
+      sfor<0, b + 1>([&](auto Lq) {
+        constexpr int l = LBM_CI(Lq);
+        constexpr double h = he_coef(a, k, c2) * he_coef(b, l, c2);
+        if constexpr (h != 0.0) acc += Real(h) * D[k][l];
+      });
+    });
+    if constexpr (!SHIFTED) {
+      constexpr double kp = kappa<L, Real>(a, b);
+      if constexpr (kp != 0.0) acc += Real(kp);
+    }
+    return acc;
+  };
+
+  const Real drho = hmom(IC<0>{}, IC<0>{});  // rho - rho_ref
+  Real rho = rho_ref + drho;
   Real ux, uy, e = Real(0);
   if constexpr (THERMAL) {
     // FP64 recovery of rho, u and theta from the energy moment 2 rho E = sum f xi^2 (Sec. II.A)
@@ -228,28 +280,12 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
     e = (Real)(c2 * (theta - 1.0));
   } else {
     const Real irho = Real(1) / rho;
-    ux = m[1][0] * irho;
-    uy = m[0][1] * irho;
+    ux = hmom(IC<1>{}, IC<0>{}) * irho;
+    uy = hmom(IC<0>{}, IC<1>{}) * irho;
   }
 
   Real A[5][5];
   equilibrium_coefficients<L, THERMAL>(rho, ux, uy, e, A);
-
-  // Hermite moments of f: M[a][b] = sum_{k<=a, l<=b} he_coef(a,k) he_coef(b,l) m[k][l]
-  auto hmom = [&](auto Aa, auto Bb) -> Real {
-    constexpr int a = LBM_CI(Aa);
-    constexpr int b = LBM_CI(Bb);
-    Real acc = Real(0);
-    sfor<0, a + 1>([&](auto K) {
-      constexpr int k = LBM_CI(K);
-      sfor<0, b + 1>([&](auto Lq) {
-        constexpr int l = LBM_CI(Lq);
-        constexpr double h = he_coef(a, k, c2) * he_coef(b, l, c2);
-        if constexpr (h != 0.0) acc += Real(h) * m[k][l];
-      });
-    });
-    return acc;
-  };
 
   Real B[5][5];
   if constexpr (COLL == COLL_PR) {
@@ -290,7 +326,7 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
     a1_fourth<L, THERMAL>(ux, uy, e, B);
   }
 
-  // --- coefficients of the rebuilt populations (Eq. GenRegCollision) ---
+  // --- coefficients of the rebuilt populations (Eq. GenRegCollision), minus the reference ---
   Real C[5][5];
   sfor<0, L::NMAX + 1>([&](auto N) {
     constexpr int n = LBM_CI(N);
@@ -299,7 +335,11 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
       constexpr int b = n - a;
       if constexpr (L::keep(a, b)) {
         constexpr double sc = 1.0 / (factorial(a) * factorial(b) * ipow(c2, a + b));
-        Real v = (n <= P.neq) ? A[a][b] : Real(0);
+        Real v;
+        if constexpr (n == 0)
+          v = drho;  // a0^(0) - rho_ref
+        else
+          v = (n <= P.neq) ? A[a][b] : Real(0);
         if constexpr (COLL == COLL_BGK) {
           v *= P.omega;
         } else if constexpr (n >= 2) {
@@ -311,19 +351,25 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
     });
   });
 
+  // plain storage: f*_i = w^_i + w_i (...); shifted: q*_i = s (f*_i / w_i - rho0) = (...)
   if constexpr (COLL == COLL_BGK) {
-    // f* = (1 - 1/tau) f + f^(0) / tau  (Sec. III.A)
-    const Real shift = SHIFTED ? -P.s * P.rho0 * P.omega : Real(0);
+    // f* - ref = (1 - 1/tau)(f - ref) + (f^(0) - ref) / tau  (Sec. III.A)
     rebuild<L, SHIFTED>(C, [&](auto I, Real acc) {
       constexpr int i = LBM_CI(I);
-      q[i] = P.om1 * q[i] + acc + shift;
+      const Real dv = P.om1 * d[i] + acc;
+      if constexpr (SHIFTED)
+        q[i] = dv;
+      else
+        q[i] = Real(ref_weight<L, Real>(i)) + dv;
     });
   } else {
     // f* = f^(0) + (1 - 1/tau) f^(1)  (Eq. RegularizedCollision)
-    const Real shift = SHIFTED ? -P.s * P.rho0 : Real(0);
     rebuild<L, SHIFTED>(C, [&](auto I, Real acc) {
       constexpr int i = LBM_CI(I);
-      q[i] = acc + shift;
+      if constexpr (SHIFTED)
+        q[i] = acc;
+      else
+        q[i] = Real(ref_weight<L, Real>(i)) + acc;
     });
   }
 }

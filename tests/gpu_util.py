@@ -74,3 +74,11 @@ def rel_l2(a, b):
 
 def max_rel(a, b):
     return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def pop_rel(got, ref, w):
+    """Per-population error of one collision, relative to the population's own magnitude or to its
+    equilibrium scale w_i (lattice weight at unit density), whichever is larger.  A population the
+    collision drives close to zero keeps the absolute resolution of its natural scale."""
+    w = np.asarray(w).reshape((-1,) + (1,) * (np.ndim(ref) - 1))
+    return float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), w)))
