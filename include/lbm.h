@@ -145,6 +145,34 @@ double lbm_tau(const lbm_ctx *c);
 int lbm_save(lbm_ctx *c, const char *path);
 int lbm_load(lbm_ctx *c, const char *path);
 
+/* Allocation-free conservation sums, for callers that cannot allocate device
+ * memory when they need them: code whose device memory is owned by another
+ * allocator (a framework pool), loops that forbid allocation after start-up,
+ * hosts that hand out buffers but no allocation rights.  The paper has no
+ * counterpart; this is a service entry point of the library.
+ *
+ * Computes the same four FP64 sums as lbm_conservation (mass, x- and
+ * y-momentum, total energy), with the same kernels, from populations the
+ * caller owns:
+ *  - f: device pointer to populations in the storage format `storage`
+ *    (LBM_F64 / LBM_F32 / LBM_F16_SHIFT / LBM_BF16_SHIFT), SoA layout
+ *    [V][ny][pitch] in the library's velocity order (lbm_lattice_info); plane
+ *    stride ny * pitch elements, pitch >= nx.  rho0 and store_scale (0 = 1)
+ *    describe shifted storage as in lbm_params.
+ *  - out4: device pointer to 4 doubles, written on `stream` (cudaStream_t,
+ *    NULL = legacy default stream); the call does not synchronize.
+ * It allocates nothing: the per-block partial sums live in a static device
+ * array of LBM_NOALLOC_MAX_CELLS / 256 * 4 doubles (2 MiB) that every GPU
+ * loading the library holds until exit.  Grids above LBM_NOALLOC_MAX_CELLS
+ * cells return LBM_EINVAL.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be ordered
+ * by the caller.  Errors: LBM_EINVAL (bad argument or size), LBM_ECUDA. */
+#define LBM_NOALLOC_MAX_CELLS 16777216LL
+int lbm_conservation_noalloc(int lattice, int storage, const void *f, int nx, int ny, int pitch, double rho0,
+                             double store_scale, double *out4, void *stream);
+
 /* Text of a status code / of the context's last failure. */
 const char *lbm_strerror(int code);
 const char *lbm_last_error(const lbm_ctx *c);

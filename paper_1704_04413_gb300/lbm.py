@@ -26,7 +26,8 @@ COLLISIONS = {"bgk": BGK, "pr": PR, "rr": RR}
 STORAGES = {"f64": F64, "f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT}
 EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_moments",
             "lbm_conservation", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
-            "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error"]
+            "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error",
+            "lbm_conservation_noalloc"]
 
 
 class lbm_params(ctypes.Structure):
@@ -72,6 +73,8 @@ def load(path: str = LIB_PATH):
         "lbm_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
+        "lbm_conservation_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -203,3 +206,13 @@ def lbm_save(ctx, path: str):
 
 def lbm_load(ctx, path: str):
     return _check(load().lbm_load(ctx, path.encode()), ctx, "lbm_load")
+
+
+def lbm_conservation_noalloc(lattice, storage, f, nx, ny, pitch, out4, rho0=0.0, store_scale=0.0, stream=None):
+    """Allocation-free conservation sums: f and out4 are device buffers the caller owns (torch CUDA tensors or
+    raw device addresses); the sums are written to out4 on `stream`."""
+    fp = f.data_ptr() if hasattr(f, "data_ptr") else f
+    op = out4.data_ptr() if hasattr(out4, "data_ptr") else out4
+    rc = load().lbm_conservation_noalloc(LATTICES.get(lattice, lattice), STORAGES.get(storage, storage), fp,
+                                         nx, ny, pitch, rho0, store_scale, op, stream)
+    return _check(rc, None, "lbm_conservation_noalloc")
