@@ -15,12 +15,23 @@
 #include <cuda_fp16.h>
 
 #include "lattice.cuh"
+#include "vec2.cuh"
 
 #define LBM_CI(X) decltype(X)::value
 
 namespace lbm {
 
 enum { COLL_BGK = 0, COLL_PR = 1, COLL_RR = 2 };
+
+// Lane type of a compute type (F2 computes two cells in FP32 lanes).
+template <class R>
+struct Scalar {
+  using type = R;
+};
+template <>
+struct Scalar<F2> {
+  using type = float;
+};
 
 template <class Real>
 struct CollParams {
@@ -146,9 +157,9 @@ __device__ __forceinline__ void rebuild(const Real (&C)[5][5], F&& emit) {
           constexpr double h = he(b, v, c2);
           if constexpr (L::keep(a, b) && h != 0.0) {
             if constexpr (b % 2 == 0)
-              ev += Real(h) * C[a][b];
+              ev = madd(Real(h), C[a][b], ev);
             else
-              od += Real(h) * C[a][b];
+              od = madd(Real(h), C[a][b], od);
           }
         });
         g[a][V + v] = ev + od;
@@ -164,7 +175,7 @@ __device__ __forceinline__ void rebuild(const Real (&C)[5][5], F&& emit) {
     sfor<0, L::NMAX + 1>([&](auto Aa) {
       constexpr int a = LBM_CI(Aa);
       constexpr double h = he(a, L::CX[i], c2) * (SHIFTED ? 1.0 : L::W[i]);
-      if constexpr (h != 0.0 && L::keep(a, 0)) acc += Real(h) * g[a][V + v];
+      if constexpr (h != 0.0 && L::keep(a, 0)) acc = madd(Real(h), g[a][V + v], acc);
     });
     emit(I, acc);
   });
@@ -199,6 +210,8 @@ __host__ __device__ constexpr double kappa(int a, int b) {
 // ---------------------------------------------------------------------------
 template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real>
 __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P) {
+  using Sc = typename Scalar<Real>::type;
+  static_assert(!(THERMAL && !__is_same(Sc, Real)), "the thermal path computes one cell per thread");
   constexpr double c2 = L::CS2;
   // highest monomial order of f the mode needs
   constexpr int PM = (COLL == COLL_PR) ? L::NMAX : (COLL == COLL_RR ? (THERMAL ? 3 : 2) : 1);
@@ -211,7 +224,7 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
     if constexpr (SHIFTED)
       d[i] = q[i];
     else
-      d[i] = q[i] - Real(ref_weight<L, Real>(i));
+      d[i] = q[i] - Real(ref_weight<L, Sc>(i));
   });
 
   // --- monomial moments of the deviations D[k][l] = sum_i d_i cx^k cy^l (Sec. II.A) ---
@@ -225,7 +238,7 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
         sfor<0, L::Q>([&](auto I) {
           constexpr int i = LBM_CI(I);
           constexpr double c = ipow(L::CX[i], k) * ipow(L::CY[i], l) * (SHIFTED ? L::W[i] : 1.0);
-          if constexpr (c != 0.0) acc += Real(c) * d[i];
+          if constexpr (c != 0.0) acc = madd(Real(c), d[i], acc);
         });
         D[k][l] = SHIFTED ? acc * P.inv_s : acc;
       }
@@ -242,11 +255,11 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
       sfor<0, b + 1>([&](auto Lq) {
         constexpr int l = LBM_CI(Lq);
         constexpr double h = he_coef(a, k, c2) * he_coef(b, l, c2);
-        if constexpr (h != 0.0) acc += Real(h) * D[k][l];
+        if constexpr (h != 0.0) acc = madd(Real(h), D[k][l], acc);
       });
     });
     if constexpr (!SHIFTED) {
-      constexpr double kp = kappa<L, Real>(a, b);
+      constexpr double kp = kappa<L, Sc>(a, b);
       if constexpr (kp != 0.0) acc += Real(kp);
     }
     return acc;
@@ -360,7 +373,7 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
       if constexpr (SHIFTED)
         q[i] = dv;
       else
-        q[i] = Real(ref_weight<L, Real>(i)) + dv;
+        q[i] = Real(ref_weight<L, Sc>(i)) + dv;
     });
   } else {
     // f* = f^(0) + (1 - 1/tau) f^(1)  (Eq. RegularizedCollision)
@@ -369,7 +382,7 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
       if constexpr (SHIFTED)
         q[i] = acc;
       else
-        q[i] = Real(ref_weight<L, Real>(i)) + acc;
+        q[i] = Real(ref_weight<L, Sc>(i)) + acc;
     });
   }
 }

@@ -31,14 +31,15 @@ struct CollParamsD {
 
 template <class Real>
 __host__ __device__ inline CollParams<Real> cast_params(const CollParamsD& d) {
+  using Sc = typename Scalar<Real>::type;
   CollParams<Real> p;
-  p.omega = (Real)d.omega;
-  p.om1 = (Real)d.om1;
+  p.omega = Real((Sc)d.omega);
+  p.om1 = Real((Sc)d.om1);
   p.neq = d.neq;
   p.nreg = d.nreg;
-  p.rho0 = (Real)d.rho0;
-  p.s = (Real)d.s;
-  p.inv_s = (Real)d.inv_s;
+  p.rho0 = Real((Sc)d.rho0);
+  p.s = Real((Sc)d.s);
+  p.inv_s = Real((Sc)d.inv_s);
   return p;
 }
 
@@ -55,47 +56,253 @@ __device__ __forceinline__ int src_coord(int x, int c, int n, int bc) {
   return s;
 }
 
-constexpr int STEP_BX = 128;
+#ifndef LBM_STEP_BX
+#define LBM_STEP_BX 128
+#endif
+#ifndef LBM_STEP_MINB_LARGE
+#define LBM_STEP_MINB_LARGE 5
+#endif
+constexpr int STEP_BX = LBM_STEP_BX;  // cells (threads) per block
 
+// Byte offsets of the pulled source of population i relative to the cell's address in plane 0,
+// (i * plane - cy_i * pitch - cx_i) * sizeof(S) (interior cells, no wrap), and of its store,
+// i * plane * sizeof(S).  Kernel parameters: they enter the address adds as constant-bank operands.
+template <int Q>
+struct PullOffsets {
+  long long src[Q];
+  long long dst[Q];
+};
+
+// Raw loads issued in program order (volatile asm keeps them ahead of the arithmetic that consumes
+// them, so all V loads of a cell are in flight together).
+template <class S>
+__device__ __forceinline__ auto ld_raw(const char* p);
+template <>
+__device__ __forceinline__ auto ld_raw<double>(const char* p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+template <>
+__device__ __forceinline__ auto ld_raw<float>(const char* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+template <>
+__device__ __forceinline__ auto ld_raw<__half>(const char* p) {
+  unsigned short u;
+  asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(u) : "l"(p));
+  return __half2float(__ushort_as_half(u));
+}
+template <>
+__device__ __forceinline__ auto ld_raw<__nv_bfloat16>(const char* p) {
+  unsigned short u;
+  asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(u) : "l"(p));
+  return __bfloat162float(__ushort_as_bfloat16(u));
+}
+
+// Registers: the D2V37 kernels are capped so that at least LBM_STEP_MINB_LARGE blocks fit on an SM.
+template <class L>
+struct StepBlocks {
+  static constexpr int MIN = L::Q > 20 ? LBM_STEP_MINB_LARGE : 1;
+};
+
+// One block = STEP_BX consecutive cells of one row; the grid is 1D over (row, column block).
 template <class L, int COLL, bool THERMAL, class Real, class S>
-__global__ void __launch_bounds__(STEP_BX) k_step(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g,
-                                                  CollParams<Real> P) {
-  const int x = blockIdx.x * STEP_BX + threadIdx.x;
+__global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
+    k_step(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<Real> P,
+           const __grid_constant__ PullOffsets<L::Q> off) {
+  const int y = blockIdx.x / nbx;
+  const int bx = blockIdx.x - y * nbx;
+  const int x = bx * STEP_BX + threadIdx.x;
   if (x >= g.nx) return;
-  for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
+  // first column of this thread's warp: the interior test is uniform across the warp
+  const int xw = bx * STEP_BX + (threadIdx.x & ~31);
+  const long long cen = (long long)y * g.pitch + x;
   Real q[L::Q];
-  sfor<0, L::Q>([&](auto I) {
-    constexpr int i = LBM_CI(I);
-    const int xs = src_coord(x, L::CX[i], g.nx, g.bcx);
-    const int ys = src_coord(y, L::CY[i], g.ny, g.bcy);
-    q[i] = (Real)Store<S>::ld(fin + (long long)i * g.plane + (long long)ys * g.pitch + xs);
-  });
-  collide<L, COLL, THERMAL, Store<S>::SHIFTED>(q, P);
-  const long long o = (long long)y * g.pitch + x;
-  sfor<0, L::Q>([&](auto I) {
-    constexpr int i = LBM_CI(I);
-    Store<S>::st(fout + (long long)i * g.plane + o, q[i]);
-  });
+  if (xw >= L::VMAX && xw + 31 + L::VMAX < g.nx && y >= L::VMAX && y + L::VMAX < g.ny) {
+    const char* c = reinterpret_cast<const char*>(fin + cen);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      q[i] = (Real)ld_raw<S>(c + off.src[i]);
+    });
+  } else {
+    const char* b = reinterpret_cast<const char*>(fin);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      const int xs = src_coord(x, L::CX[i], g.nx, g.bcx);
+      const int ys = src_coord(y, L::CY[i], g.ny, g.bcy);
+      q[i] = (Real)ld_raw<S>(b + off.dst[i] + ((long long)ys * g.pitch + xs) * (long long)sizeof(S));
+    });
   }
+  collide<L, COLL, THERMAL, Store<S>::SHIFTED>(q, P);
+  char* o = reinterpret_cast<char*>(fout + cen);
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    Store<S>::st(reinterpret_cast<S*>(o + off.dst[i]), q[i]);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Two cells per thread.  Thread t of a block handles columns x = 2t, 2t + 1 of its row; the
+// arithmetic runs on both at once in packed FP32x2 (vec2.cuh).  A population whose x-velocity
+// is even is pulled with one 8-byte (FP32) or 4-byte (FP16/BF16) aligned load for both cells,
+// an odd one with two scalar loads; every store is one aligned pair.
+// ---------------------------------------------------------------------------
+#ifndef LBM_STEP_PAIRS
+#define LBM_STEP_PAIRS 1
+#endif
+#ifndef LBM_STEP2_MINB_LARGE
+#define LBM_STEP2_MINB_LARGE 2
+#endif
+
+template <class S>
+__device__ __forceinline__ F2 ld_pair(const char* p);
+template <>
+__device__ __forceinline__ F2 ld_pair<float>(const char* p) {
+  float a, b;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p));
+  return F2(a, b);
+}
+template <>
+__device__ __forceinline__ F2 ld_pair<__half>(const char* p) {
+  unsigned u;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(p));
+  __half2 h = *reinterpret_cast<__half2*>(&u);
+  return F2(__half22float2(h));
+}
+template <>
+__device__ __forceinline__ F2 ld_pair<__nv_bfloat16>(const char* p) {
+  unsigned u;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(p));
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+  return F2(__bfloat1622float2(h));
+}
+
+template <class S>
+__device__ __forceinline__ void st_pair(S* p, F2 v);
+template <>
+__device__ __forceinline__ void st_pair<float>(float* p, F2 v) {
+  *reinterpret_cast<float2*>(p) = v.v;
+}
+template <>
+__device__ __forceinline__ void st_pair<__half>(__half* p, F2 v) {
+  *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.v.x, v.v.y);
+}
+template <>
+__device__ __forceinline__ void st_pair<__nv_bfloat16>(__nv_bfloat16* p, F2 v) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.v.x, v.v.y);
+}
+
+template <class L>
+struct Step2Blocks {
+  static constexpr int MIN = L::Q > 20 ? LBM_STEP2_MINB_LARGE : 1;
+};
+
+template <class L, int COLL, class S>
+__global__ void __launch_bounds__(STEP_BX, Step2Blocks<L>::MIN)
+    k_step2(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<F2> P,
+            const __grid_constant__ PullOffsets<L::Q> off) {
+  const int y = blockIdx.x / nbx;
+  const int bx = blockIdx.x - y * nbx;
+  const int x = 2 * (bx * STEP_BX + threadIdx.x);
+  if (x >= g.nx) return;
+  const bool two = x + 1 < g.nx;
+  const int xw = 2 * (bx * STEP_BX + (threadIdx.x & ~31));  // first column of the warp's 64
+  const long long cen = (long long)y * g.pitch + x;
+  F2 q[L::Q];
+  if (xw >= L::VMAX && xw + 63 + L::VMAX < g.nx && y >= L::VMAX && y + L::VMAX < g.ny) {
+    const char* c = reinterpret_cast<const char*>(fin + cen);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      if constexpr (L::CX[i] % 2 == 0) {
+        q[i] = ld_pair<S>(c + off.src[i]);
+      } else {
+        const float a = ld_raw<S>(c + off.src[i]);
+        const float b = ld_raw<S>(c + off.src[i] + (long long)sizeof(S));
+        q[i] = F2(a, b);
+      }
+    });
+  } else {
+    const char* b = reinterpret_cast<const char*>(fin);
+    const int x1 = two ? x + 1 : x;  // a missing second cell repeats the first; it is not stored
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      const int ys = src_coord(y, L::CY[i], g.ny, g.bcy);
+      const int xs0 = src_coord(x, L::CX[i], g.nx, g.bcx);
+      const int xs1 = src_coord(x1, L::CX[i], g.nx, g.bcx);
+      const long long row = (long long)ys * g.pitch;
+      const float a = ld_raw<S>(b + off.dst[i] + (row + xs0) * (long long)sizeof(S));
+      const float c = ld_raw<S>(b + off.dst[i] + (row + xs1) * (long long)sizeof(S));
+      q[i] = F2(a, c);
+    });
+  }
+  collide<L, COLL, false, Store<S>::SHIFTED>(q, P);
+  char* o = reinterpret_cast<char*>(fout + cen);
+  if (two) {
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), q[i]);
+    });
+  } else {
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      Store<S>::st(reinterpret_cast<S*>(o + off.dst[i]), q[i].v.x);
+    });
+  }
+}
+
+template <class L, int COLL, class S>
+inline cudaError_t launch_step2_t(const void* fin, void* fout, const StepGeom& g, const CollParamsD& pd,
+                                  cudaStream_t st) {
+  PullOffsets<L::Q> off;
+  for (int i = 0; i < L::Q; ++i) {
+    off.dst[i] = (long long)i * g.plane * (long long)sizeof(S);
+    off.src[i] = off.dst[i] - ((long long)L::CY[i] * g.pitch + L::CX[i]) * (long long)sizeof(S);
+  }
+  const int nbx = (g.nx + 2 * STEP_BX - 1) / (2 * STEP_BX);
+  const long long nblocks = (long long)nbx * g.ny;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_step2<L, COLL, S><<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
+                                                                 cast_params<F2>(pd), off);
+  return cudaGetLastError();
 }
 
 template <class L, int COLL, bool THERMAL, class Real, class S>
 inline cudaError_t launch_step_t(const void* fin, void* fout, const StepGeom& g, const CollParamsD& pd,
                                  cudaStream_t st) {
-  dim3 grid((g.nx + STEP_BX - 1) / STEP_BX, g.ny < 65535 ? g.ny : 65535);
+  PullOffsets<L::Q> off;
+  for (int i = 0; i < L::Q; ++i) {
+    off.dst[i] = (long long)i * g.plane * (long long)sizeof(S);
+    off.src[i] = off.dst[i] - ((long long)L::CY[i] * g.pitch + L::CX[i]) * (long long)sizeof(S);
+  }
+  const int nbx = (g.nx + STEP_BX - 1) / STEP_BX;
+  const long long nblocks = (long long)nbx * g.ny;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_step<L, COLL, THERMAL, Real, S>
-      <<<grid, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, cast_params<Real>(pd));
+      <<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, cast_params<Real>(pd), off);
   return cudaGetLastError();
 }
 
 template <class L, int COLL, bool THERMAL>
 inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const StepGeom& g,
                                     const CollParamsD& pd, cudaStream_t st) {
-  switch (prec) {
-    case PREC_F64: return launch_step_t<L, COLL, THERMAL, double, double>(fin, fout, g, pd, st);
-    case PREC_F32: return launch_step_t<L, COLL, THERMAL, float, float>(fin, fout, g, pd, st);
-    case PREC_F16: return launch_step_t<L, COLL, THERMAL, float, __half>(fin, fout, g, pd, st);
-    case PREC_BF16: return launch_step_t<L, COLL, THERMAL, float, __nv_bfloat16>(fin, fout, g, pd, st);
+  // two cells per thread pay off while the pair's registers stay low (D2Q9, D2V17); D2V37 keeps one
+  if constexpr (!THERMAL && LBM_STEP_PAIRS && L::Q <= 20) {
+    switch (prec) {
+      case PREC_F64: return launch_step_t<L, COLL, THERMAL, double, double>(fin, fout, g, pd, st);
+      case PREC_F32: return launch_step2_t<L, COLL, float>(fin, fout, g, pd, st);
+      case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st);
+      case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st);
+    }
+  } else {
+    switch (prec) {
+      case PREC_F64: return launch_step_t<L, COLL, THERMAL, double, double>(fin, fout, g, pd, st);
+      case PREC_F32: return launch_step_t<L, COLL, THERMAL, float, float>(fin, fout, g, pd, st);
+      case PREC_F16: return launch_step_t<L, COLL, THERMAL, float, __half>(fin, fout, g, pd, st);
+      case PREC_BF16: return launch_step_t<L, COLL, THERMAL, float, __nv_bfloat16>(fin, fout, g, pd, st);
+    }
   }
   return cudaErrorInvalidValue;
 }
