@@ -37,7 +37,7 @@ from paper_1704_04413_gb300 import workloads as wl  # noqa: E402
 GRID = 1024
 RE, MACH = 3e4, 0.1
 LATTICES = (("D2Q9", 2), ("D2V17", 3), ("D2V37", 4))
-BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "i16": 2}
 METRIC = "RR stream-collide GLUPS & HBM-roofline fraction per lattice; low-prec vs FP32"
 REF_BAND = 128  # rows of the oracle's sample band
 PROFILE = os.path.join(ROOT, "profiles", "step_d2v37_rr_f32_1024.txt")
@@ -260,6 +260,8 @@ def run_ours(args, rank, world, local_rank):
                                           "vs_f32": round(glups / per_lattice[name]["f32"]["glups"], 3)}
             lbm.lbm_destroy(ctx)
 
+    accuracy = accuracy_vs_f64(st)
+
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -270,10 +272,49 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
                              "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
+            "accuracy_vs_f64_gpu": accuracy,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(min_seconds=10.0)
         print(json.dumps(line), flush=True)
+
+
+def vorticity(ux, uy):
+    """omega = d_x u_y - d_y u_x, fourth-order centred differences, periodic (Sec. III.B)."""
+    def d(g, axis):
+        return (-np.roll(g, -2, axis) + 8 * np.roll(g, -1, axis) - 8 * np.roll(g, 1, axis)
+                + np.roll(g, 2, axis)) / 12.0
+    return d(uy, 1) - d(ux, 0)
+
+
+def accuracy_vs_f64(stream, L=256, storages=("f32", "f16", "bf16", "i16")):
+    """Relative L2 error of vorticity (and of rho, u) after one convective time t_c = L/u0 of the
+    shear layer, each storage format against the FP64 GPU run of the same lattice."""
+    from paper_1704_04413_gb300 import lbm
+    out = {}
+    for name, neq in LATTICES:
+        V, cs2, nu, fl = shear_fields(name, L)
+        u0, _, steps = wl.shear_layer_params(L, np.sqrt(cs2), MACH, RE)
+        res = {}
+        for storage in ("f64",) + tuple(storages):
+            p = lbm.make_params(name, L, L, nu=nu, collision="rr", hermite_order=neq, storage=storage, stream=stream)
+            ctx = lbm.lbm_create(p)
+            lbm.lbm_init(ctx, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+            lbm.lbm_step(ctx, steps)
+            r, u, v = (np.empty((L, L)) for _ in range(3))
+            lbm.lbm_moments(ctx, r, u, v)
+            lbm.lbm_destroy(ctx)
+            res[storage] = (r, u, v, vorticity(u, v))
+        r0, u0_, v0, w0 = res["f64"]
+        out[name] = {"steps": steps, "grid": L}
+        for storage in storages:
+            r, u, v, w = res[storage]
+            ok = bool(np.all(np.isfinite(w)))
+            out[name][storage] = {
+                "vorticity_rel_l2": float(np.linalg.norm(w - w0) / np.linalg.norm(w0)) if ok else None,
+                "u_rel_l2": float(np.linalg.norm(np.hypot(u - u0_, v - v0)) / np.linalg.norm(np.hypot(u0_, v0))) if ok else None,
+                "rho_rel_l2": float(np.linalg.norm(r - r0) / np.linalg.norm(r0)) if ok else None}
+    return out
 
 
 def oracle_sample_step(pairs):

@@ -53,6 +53,7 @@ extern "C" {
 #define LBM_F32 1
 #define LBM_F16_SHIFT 2  /* binary16 of g_i = (f_i / w_i - rho0) * s */
 #define LBM_BF16_SHIFT 3 /* bfloat16 of the same shifted deviation */
+#define LBM_I16_SHIFT 4  /* 16-bit fixed point round(2^15 g) of the same g, |g| < 1 (saturating) */
 
 /* status codes */
 #define LBM_OK 0
@@ -75,7 +76,7 @@ typedef struct {
   double nu;         /* kinematic viscosity; used when tau <= 0: tau = nu / cs^2 + 1/2 */
   double tau;        /* relaxation time of the discrete scheme (the shifted tau-bar of Sec. III.A), > 1/2 */
   int bc_x, bc_y;    /* LBM_PERIODIC or LBM_ZERO_GRADIENT */
-  int storage;       /* LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT */
+  int storage;       /* LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT, LBM_I16_SHIFT */
   int compute;       /* LBM_F64 (requires storage LBM_F64) or LBM_F32 (any other storage) */
   double rho0;       /* shifted storage reference density; 0 = 1 */
   double store_scale;/* shifted storage scale s, a power of two; 0 = 1 */
@@ -155,7 +156,7 @@ int lbm_load(lbm_ctx *c, const char *path);
  * y-momentum, total energy), with the same kernels, from populations the
  * caller owns:
  *  - f: device pointer to populations in the storage format `storage`
- *    (LBM_F64 / LBM_F32 / LBM_F16_SHIFT / LBM_BF16_SHIFT), SoA layout
+ *    (LBM_F64 / LBM_F32 / LBM_F16_SHIFT / LBM_BF16_SHIFT / LBM_I16_SHIFT), SoA layout
  *    [V][ny][pitch] in the library's velocity order (lbm_lattice_info); plane
  *    stride ny * pitch elements, pitch >= nx.  rho0 and store_scale (0 = 1)
  *    describe shifted storage as in lbm_params.

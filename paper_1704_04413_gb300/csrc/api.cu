@@ -1,6 +1,8 @@
 // C ABI of liblbm (include/lbm.h): context management, host/device transfer,
 // time stepping and diagnostics.  Every computation is a kernel of this
 // library; this file only validates, allocates, copies and launches.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -11,7 +13,17 @@
 
 #include "../../include/lbm.h"
 #include "fields.h"
-#include "step.cuh"
+#include "step_tma.cuh"
+
+#ifndef LBM_USE_TMA
+#define LBM_USE_TMA 0
+#endif
+#ifndef LBM_ROW_PAD_BYTES
+#define LBM_ROW_PAD_BYTES 0  // extra bytes per row (a multiple of 128)
+#endif
+#ifndef LBM_PLANE_PAD_BYTES
+#define LBM_PLANE_PAD_BYTES 0  // extra bytes between population planes (a multiple of 128)
+#endif
 
 using namespace lbm;
 
@@ -28,8 +40,11 @@ struct lbm_ctx {
   int cur = 0;
   double* scratch = nullptr;  // 8 * ncells doubles, for host transfers and diagnostics
   double* partials = nullptr;
-  double* out4 = nullptr;     // device
-  double* host4 = nullptr;    // pinned host
+  double* out4 = nullptr;     // device: 4 sums, then the error word
+  double* host4 = nullptr;    // pinned host copy of the same
+  int* dev_err = nullptr;     // device error word (kernels record LBM_ETIMEOUT there)
+  bool use_tma = false;
+  CUtensorMap tmap[2];        // TMA descriptors of buf[0], buf[1]
   long long steps = 0;
   cudaStream_t st = nullptr;
   int device = 0;
@@ -82,14 +97,65 @@ cudaError_t launch_step(lbm_ctx* c, const void* fin, void* fout) {
   pd.s = c->s;
   pd.inv_s = 1.0 / c->s;
   const int coll = c->p.collision;
+    const void* tm = c->use_tma ? (const void*)&c->tmap[fin == c->buf[0] ? 0 : 1] : nullptr;
   switch (c->p.lattice) {
-    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->st);
-    case LBM_D2V17: return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, c->st);
+    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st);
+    case LBM_D2V17: return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st);
     case LBM_D2V37:
-      return c->p.thermal ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, c->st)
-                          : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, c->st);
+      return c->p.thermal ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st)
+                          : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st);
   }
   return cudaErrorInvalidValue;
+}
+
+// Box of the TMA kernel that serves (lattice, storage) and the element size.
+template <class L>
+bool tma_box_l(int prec, int* boxw, int* boxh, int* esz) {
+  constexpr bool PAIR = L::Q <= 20;
+  switch (prec) {
+    case PREC_F32: *boxw = TmaCfg<L, float, PAIR>::BOXW; *boxh = TmaCfg<L, float, PAIR>::BY; *esz = 4; return true;
+    case PREC_F16: *boxw = TmaCfg<L, __half, PAIR>::BOXW; *boxh = TmaCfg<L, __half, PAIR>::BY; *esz = 2; return true;
+    case PREC_BF16:
+      *boxw = TmaCfg<L, __nv_bfloat16, PAIR>::BOXW; *boxh = TmaCfg<L, __nv_bfloat16, PAIR>::BY; *esz = 2; return true;
+    case PREC_I16: *boxw = TmaCfg<L, short, PAIR>::BOXW; *boxh = TmaCfg<L, short, PAIR>::BY; *esz = 2; return true;
+  }
+  return false;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor maps [V][ny][pitch] of both population buffers for the TMA kernels; false leaves the
+// register-pull kernels in use.
+bool make_tensor_maps(lbm_ctx* c) {
+  if (!LBM_USE_TMA || c->p.thermal || c->prec == PREC_F64) return false;
+  int boxw = 0, boxh = 0, esz = 0;
+  bool ok = c->p.lattice == LBM_D2Q9    ? tma_box_l<D2Q9>(c->prec, &boxw, &boxh, &esz)
+            : c->p.lattice == LBM_D2V17 ? tma_box_l<D2V17>(c->prec, &boxw, &boxh, &esz)
+                                        : tma_box_l<D2V37>(c->prec, &boxw, &boxh, &esz);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!ok || !enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny, (cuuint64_t)c->V};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->g.pitch * esz, (cuuint64_t)c->g.plane * esz};
+  const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (int b = 0; b < 2; ++b) {
+    if (enc(&c->tmap[b], dt, 3, c->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 int ensure_scratch(lbm_ctx* c) {
@@ -134,6 +200,7 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->scratch);
   cudaFree(c->partials);
   cudaFree(c->out4);
+  cudaFree(c->dev_err);
   cudaFreeHost(c->host4);
   delete c;
 }
@@ -160,6 +227,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     prec = PREC_F16;
   else if (p->compute == LBM_F32 && p->storage == LBM_BF16_SHIFT)
     prec = PREC_BF16;
+  else if (p->compute == LBM_F32 && p->storage == LBM_I16_SHIFT)
+    prec = PREC_I16;
   else
     return LBM_EINVAL;
   double cs2 = 0;
@@ -188,22 +257,25 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
   c->tau = tau;
   c->rho0 = rho0;
   c->s = s;
-  c->elem = prec == PREC_F64 ? 8 : prec == PREC_F32 ? 4 : 2;
+  c->elem = prec == PREC_F64 ? 8 : prec == PREC_F32 ? 4 : 2;  // the three 16-bit formats
   c->st = (cudaStream_t)p->stream;
-  const size_t row_bytes = ((size_t)p->nx * c->elem + 127) / 128 * 128;  // rows start on 128-byte lines
+  const size_t row_bytes = ((size_t)p->nx * c->elem + 127) / 128 * 128 + LBM_ROW_PAD_BYTES;  // 128-byte lines
   c->g.pitch = (int)(row_bytes / c->elem);
-  c->g.plane = (long long)c->g.pitch * p->ny;
+  c->g.plane = (long long)c->g.pitch * p->ny + LBM_PLANE_PAD_BYTES / (long long)c->elem;
   c->g.nx = p->nx;
   c->g.ny = p->ny;
   c->g.bcx = p->bc_x;
   c->g.bcy = p->bc_y;
+  c->g.nsm = 1;
+  cudaDeviceGetAttribute(&c->g.nsm, cudaDevAttrMultiProcessorCount, c->device);
   const size_t bytes = (size_t)c->V * (size_t)c->g.plane * c->elem;
   int rc = LBM_OK;
   cudaError_t e;
   if ((e = cudaMalloc(&c->buf[0], bytes)) != cudaSuccess || (e = cudaMalloc(&c->buf[1], bytes)) != cudaSuccess ||
       (e = cudaMalloc(&c->partials, sizeof(double) * (size_t)lbm_partials_count(c->g))) != cudaSuccess ||
-      (e = cudaMalloc(&c->out4, 4 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&c->host4, 4 * sizeof(double))) != cudaSuccess) {
+      (e = cudaMalloc(&c->out4, 5 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->dev_err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMallocHost(&c->host4, 5 * sizeof(double))) != cudaSuccess) {
     rc = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
     cudaGetLastError();
     lbm_destroy(c);
@@ -211,10 +283,12 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
   }
   // padding columns are never read by a kernel; clear them once for deterministic checkpoints
   if ((e = cudaMemsetAsync(c->buf[0], 0, bytes, c->st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->buf[1], 0, bytes, c->st)) != cudaSuccess) {
+      (e = cudaMemsetAsync(c->buf[1], 0, bytes, c->st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->st)) != cudaSuccess) {
     lbm_destroy(c);
     return LBM_ECUDA;
   }
+  c->use_tma = make_tensor_maps(c);
   *out = c;
   return LBM_OK;
 }
@@ -297,7 +371,9 @@ int lbm_conservation(lbm_ctx* c, double out[4]) {
   LBM_CK(c, lbm_launch_conservation(c->p.lattice, c->prec, c->buf[c->cur], c->g, c->rho0, 1.0 / c->s, c->partials,
                                     c->out4, c->st));
   LBM_CK(c, cudaMemcpyAsync(c->host4, c->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  LBM_CK(c, cudaMemcpyAsync(c->host4 + 4, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   LBM_CK(c, cudaStreamSynchronize(c->st));
+  if (*reinterpret_cast<int*>(c->host4 + 4) != 0) return fail(c, LBM_ETIMEOUT, "a step kernel's bounded wait ran out");
   bool finite = true;
   for (int k = 0; k < 4; ++k) {
     out[k] = c->host4[k];
@@ -318,7 +394,9 @@ int lbm_diagnostics(lbm_ctx* c, double out[4]) {
                                nullptr, c->st));
   LBM_CK(c, lbm_launch_diagnostics(ux, uy, c->g, c->partials, c->out4, c->st));
   LBM_CK(c, cudaMemcpyAsync(c->host4, c->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  LBM_CK(c, cudaMemcpyAsync(c->host4 + 4, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   LBM_CK(c, cudaStreamSynchronize(c->st));
+  if (*reinterpret_cast<int*>(c->host4 + 4) != 0) return fail(c, LBM_ETIMEOUT, "a step kernel's bounded wait ran out");
   const double inv = 1.0 / (double)n;
   const double m0 = c->host4[0] * inv, m1 = c->host4[2] * inv;
   const double v0 = c->host4[1] * inv - m0 * m0, v1 = c->host4[3] * inv - m1 * m1;

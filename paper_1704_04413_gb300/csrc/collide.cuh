@@ -75,6 +75,20 @@ struct Store<__nv_bfloat16> {
   __device__ static __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   __device__ static __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
+// 16-bit fixed point of the shifted deviation: n = round(2^15 g), g in [-1, 1) (saturating).  Uniform
+// absolute resolution 2^-15 / s of f_i / w_i, where binary16 resolves only 2^-12 at |g| ~ 0.3.
+constexpr float kFix16 = 32768.0f;
+__device__ __forceinline__ short fix16_encode(float v) {
+  int n = __float2int_rn(v * kFix16);
+  n = n < -32768 ? -32768 : (n > 32767 ? 32767 : n);
+  return (short)n;
+}
+template <>
+struct Store<short> {
+  static constexpr bool SHIFTED = true;
+  __device__ static __forceinline__ float ld(const short* p) { return (float)__ldg(p) * (1.0f / kFix16); }
+  __device__ static __forceinline__ void st(short* p, float v) { *p = fix16_encode(v); }
+};
 
 // ---------------------------------------------------------------------------
 // Equilibrium coefficients a0 (App. B recursion specialised to 2D):

@@ -257,6 +257,7 @@ static cudaError_t init_l(int prec, const double* rho, const double* ux, const d
     case PREC_F32: return init_t<L, float>(rho, ux, uy, th, grad, f, g, ip, st);
     case PREC_F16: return init_t<L, __half>(rho, ux, uy, th, grad, f, g, ip, st);
     case PREC_BF16: return init_t<L, __nv_bfloat16>(rho, ux, uy, th, grad, f, g, ip, st);
+    case PREC_I16: return init_t<L, short>(rho, ux, uy, th, grad, f, g, ip, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -275,6 +276,7 @@ static cudaError_t init_l(int prec, const double* rho, const double* ux, const d
     case PREC_F32: return FN<L, float>(__VA_ARGS__);           \
     case PREC_F16: return FN<L, __half>(__VA_ARGS__);          \
     case PREC_BF16: return FN<L, __nv_bfloat16>(__VA_ARGS__);  \
+    case PREC_I16: return FN<L, short>(__VA_ARGS__);           \
   }                                                            \
   return cudaErrorInvalidValue;
 

@@ -63,6 +63,7 @@ extern "C" int lbm_conservation_noalloc(int lattice, int storage, const void* f,
     case LBM_F32: prec = lbm::PREC_F32; break;
     case LBM_F16_SHIFT: prec = lbm::PREC_F16; break;
     case LBM_BF16_SHIFT: prec = lbm::PREC_BF16; break;
+    case LBM_I16_SHIFT: prec = lbm::PREC_I16; break;
     default: return LBM_EINVAL;
   }
   const double r0 = rho0 == 0 ? 1.0 : rho0;

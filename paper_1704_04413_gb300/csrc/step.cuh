@@ -9,18 +9,21 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "collide.cuh"
 
 namespace lbm {
 
 enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1 };
-enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3 };
+enum { PREC_F64 = 0, PREC_F32 = 1, PREC_F16 = 2, PREC_BF16 = 3, PREC_I16 = 4 };
 
 struct StepGeom {
   long long plane;  // elements per population plane (ny * pitch)
   int pitch;        // elements per row
   int nx, ny;
   int bcx, bcy;
+  int nsm;          // SMs of the device (persistent grids)
 };
 
 struct CollParamsD {
@@ -101,6 +104,12 @@ __device__ __forceinline__ auto ld_raw<__nv_bfloat16>(const char* p) {
   asm volatile("ld.global.nc.b16 %0, [%1];" : "=h"(u) : "l"(p));
   return __bfloat162float(__ushort_as_bfloat16(u));
 }
+template <>
+__device__ __forceinline__ auto ld_raw<short>(const char* p) {
+  short u;
+  asm volatile("ld.global.nc.s16 %0, [%1];" : "=h"(u) : "l"(p));
+  return (float)u * (1.0f / kFix16);
+}
 
 // Registers: the D2V37 kernels are capped so that at least LBM_STEP_MINB_LARGE blocks fit on an SM.
 template <class L>
@@ -173,6 +182,13 @@ __device__ __forceinline__ F2 ld_pair<__half>(const char* p) {
   return F2(__half22float2(h));
 }
 template <>
+__device__ __forceinline__ F2 ld_pair<short>(const char* p) {
+  unsigned u;
+  asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(p));
+  const float a = (float)(short)(u & 0xffffu), b = (float)(short)(u >> 16);
+  return F2(a, b) * F2(1.0f / kFix16);
+}
+template <>
 __device__ __forceinline__ F2 ld_pair<__nv_bfloat16>(const char* p) {
   unsigned u;
   asm volatile("ld.global.nc.b32 %0, [%1];" : "=r"(u) : "l"(p));
@@ -189,6 +205,11 @@ __device__ __forceinline__ void st_pair<float>(float* p, F2 v) {
 template <>
 __device__ __forceinline__ void st_pair<__half>(__half* p, F2 v) {
   *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.v.x, v.v.y);
+}
+template <>
+__device__ __forceinline__ void st_pair<short>(short* p, F2 v) {
+  const unsigned lo = (unsigned short)fix16_encode(v.v.x), hi = (unsigned short)fix16_encode(v.v.y);
+  *reinterpret_cast<unsigned*>(p) = lo | (hi << 16);
 }
 template <>
 __device__ __forceinline__ void st_pair<__nv_bfloat16>(__nv_bfloat16* p, F2 v) {
@@ -295,6 +316,7 @@ inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const
       case PREC_F32: return launch_step2_t<L, COLL, float>(fin, fout, g, pd, st);
       case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st);
       case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st);
+      case PREC_I16: return launch_step2_t<L, COLL, short>(fin, fout, g, pd, st);
     }
   } else {
     switch (prec) {
@@ -302,6 +324,7 @@ inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const
       case PREC_F32: return launch_step_t<L, COLL, THERMAL, float, float>(fin, fout, g, pd, st);
       case PREC_F16: return launch_step_t<L, COLL, THERMAL, float, __half>(fin, fout, g, pd, st);
       case PREC_BF16: return launch_step_t<L, COLL, THERMAL, float, __nv_bfloat16>(fin, fout, g, pd, st);
+      case PREC_I16: return launch_step_t<L, COLL, THERMAL, float, short>(fin, fout, g, pd, st);
     }
   }
   return cudaErrorInvalidValue;
@@ -320,12 +343,12 @@ inline cudaError_t launch_step_lattice(int coll, int prec, const void* fin, void
 
 }  // namespace lbm
 
-// One translation unit per lattice instantiates its kernels behind these.
-cudaError_t lbm_launch_step_d2q9(int coll, int prec, const void* fin, void* fout, const lbm::StepGeom& g,
-                                 const lbm::CollParamsD& pd, cudaStream_t st);
-cudaError_t lbm_launch_step_d2v17(int coll, int prec, const void* fin, void* fout, const lbm::StepGeom& g,
-                                  const lbm::CollParamsD& pd, cudaStream_t st);
-cudaError_t lbm_launch_step_d2v37(int coll, int prec, const void* fin, void* fout, const lbm::StepGeom& g,
-                                  const lbm::CollParamsD& pd, cudaStream_t st);
-cudaError_t lbm_launch_step_d2v37_thermal(int coll, int prec, const void* fin, void* fout, const lbm::StepGeom& g,
-                                          const lbm::CollParamsD& pd, cudaStream_t st);
+// One translation unit per lattice instantiates its kernels behind these.  `tmap` (a CUtensorMap of
+// the input buffer) selects the TMA-staged kernels for the FP32 and 16-bit formats when not NULL.
+#define LBM_STEP_LAUNCHER_ARGS                                                                      \
+  int coll, int prec, const void *fin, void *fout, const lbm::StepGeom &g, const lbm::CollParamsD &pd, \
+      const void *tmap, int *err, cudaStream_t st
+cudaError_t lbm_launch_step_d2q9(LBM_STEP_LAUNCHER_ARGS);
+cudaError_t lbm_launch_step_d2v17(LBM_STEP_LAUNCHER_ARGS);
+cudaError_t lbm_launch_step_d2v37(LBM_STEP_LAUNCHER_ARGS);
+cudaError_t lbm_launch_step_d2v37_thermal(LBM_STEP_LAUNCHER_ARGS);

@@ -1,7 +1,6 @@
 // Stream-and-collide kernels of the D2Q9 lattice (isothermal).
-#include "step.cuh"
+#include "step_tma.cuh"
 
-cudaError_t lbm_launch_step_d2q9(int coll, int prec, const void* fin, void* fout, const lbm::StepGeom& g,
-                                 const lbm::CollParamsD& pd, cudaStream_t st) {
-  return lbm::launch_step_lattice<lbm::D2Q9, false>(coll, prec, fin, fout, g, pd, st);
+cudaError_t lbm_launch_step_d2q9(LBM_STEP_LAUNCHER_ARGS) {
+  return lbm::launch_step_any<lbm::D2Q9, false>(coll, prec, fin, fout, g, pd, tmap, err, st);
 }

@@ -18,12 +18,12 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 D2Q9, D2V17, D2V37 = 0, 1, 2
 BGK, PR, RR = 0, 1, 2
 PERIODIC, ZERO_GRADIENT = 0, 1
-F64, F32, F16_SHIFT, BF16_SHIFT = 0, 1, 2, 3
+F64, F32, F16_SHIFT, BF16_SHIFT, I16_SHIFT = 0, 1, 2, 3, 4
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EIO = 0, -1, -2, -3, -4, -5, -6
 
 LATTICES = {"D2Q9": D2Q9, "D2V17": D2V17, "D2V37": D2V37}
 COLLISIONS = {"bgk": BGK, "pr": PR, "rr": RR}
-STORAGES = {"f64": F64, "f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT}
+STORAGES = {"f64": F64, "f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT, "i16": I16_SHIFT}
 EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_moments",
             "lbm_conservation", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
             "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error",

@@ -1,0 +1,60 @@
+"""Whole-scheme runs on the GPU against closed-form physics and the oracle.
+
+* Sod shock tubes of Sec. III.C (D2V37, thermal, RR-4 and PR-4): GPU density against the oracle's
+  and against the exact gamma = 2 Riemann solution.
+* Viscous decay of a shear wave (Sec. III.A, nu = cs^2 (tau - 1/2)) on every lattice.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from oracle import riemann
+from paper_1704_04413_gb300 import workloads as wl
+
+from gpu_util import Ctx, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def sod_setup(PL, RL, frac, Lx=400):
+    L = orc.lattice("D2V37")
+    TL, TR = PL / RL, 1.0
+    s = 1.0 / max(TL, TR)  # the hottest initial state sits at theta = 1
+    left, right = (RL, 0.0, TL * s), (1.0, 0.0, TR * s)
+    nx = 2 * Lx
+    T = int(round(frac * Lx / np.sqrt(2.0 * L.cs2 * TR * s)))
+    fl = wl.riemann_tube(nx, 1, left, right, Lx)
+    xs = np.arange(nx) - Lx / 2 + 0.5
+    sel = (xs >= 0) & (xs <= Lx)
+    ex = riemann.sample((RL, 0.0, RL * L.cs2 * left[2]), (1.0, 0.0, L.cs2 * right[2]), 2.0, (xs[sel] - Lx / 2) / T)[0]
+    return fl, T, sel, ex, nx
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 2e-4)])
+@pytest.mark.parametrize("PL,RL,tau,frac", [(10.0, 8.0, 0.595, 0.2), (10.0, 2.0, 0.760, 0.1)])
+def test_sod_tube_rr_matches_oracle_and_exact(PL, RL, tau, frac, storage, tol):
+    fl, T, sel, ex, nx = sod_setup(PL, RL, frac)
+    op = orc.params("D2V37", nx, 1, tau, "rr", 4, thermal=True)
+    r_o = orc.moments(op, orc.step(op, orc.init(op, fl.rho, fl.ux, fl.uy, fl.theta), T))[0][0]
+    with Ctx("D2V37", nx, 1, tau, "rr", 4, 0, storage, thermal=True) as c:
+        c.init(fl, fl.theta, grad=False)
+        c.step(T)
+        r = c.moments()[0][0]
+    assert rel_l2(r, r_o) <= tol
+    assert np.abs(r[sel] - ex).sum() / np.abs(ex).sum() < 0.015
+
+
+@pytest.mark.parametrize("name,neq", [("D2Q9", 2), ("D2V17", 3), ("D2V37", 4)])
+def test_shear_wave_decay_on_gpu(name, neq):
+    L = orc.lattice(name)
+    nx, ny, tau, amp = 4, 64, 0.8, 1e-4
+    nu = L.cs2 * (tau - 0.5)
+    k = 2 * np.pi / ny
+    T = int(round(np.log(2) / (nu * k * k)))
+    fl = wl.shear_wave(nx, ny, amp)
+    with Ctx(name, nx, ny, tau, "rr", neq, 0, "f64") as c:
+        c.init(fl)
+        c.step(T)
+        ux = c.moments()[1]
+    A = 2.0 / ny * np.sum(ux[:, 0] * np.sin(k * np.arange(ny)))
+    assert abs(A / (amp * np.exp(-nu * k * k * T)) - 1.0) < 0.01
