@@ -1,8 +1,6 @@
 // C ABI of liblbm (include/lbm.h): context management, host/device transfer,
 // time stepping and diagnostics.  Every computation is a kernel of this
 // library; this file only validates, allocates, copies and launches.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -13,17 +11,8 @@
 
 #include "../../include/lbm.h"
 #include "fields.h"
-#include "step_tma.cuh"
+#include "step.cuh"
 
-#ifndef LBM_USE_TMA
-#define LBM_USE_TMA 0
-#endif
-#ifndef LBM_ROW_PAD_BYTES
-#define LBM_ROW_PAD_BYTES 0  // extra bytes per row (a multiple of 128)
-#endif
-#ifndef LBM_PLANE_PAD_BYTES
-#define LBM_PLANE_PAD_BYTES 0  // extra bytes between population planes (a multiple of 128)
-#endif
 
 using namespace lbm;
 
@@ -42,9 +31,7 @@ struct lbm_ctx {
   double* partials = nullptr;
   double* out4 = nullptr;     // device: 4 sums, then the error word
   double* host4 = nullptr;    // pinned host copy of the same
-  int* dev_err = nullptr;     // device error word (kernels record LBM_ETIMEOUT there)
-  bool use_tma = false;
-  CUtensorMap tmap[2];        // TMA descriptors of buf[0], buf[1]
+  int* dev_err = nullptr;     // device error word (bounded device waits record LBM_ETIMEOUT there)
   long long steps = 0;
   cudaStream_t st = nullptr;
   int device = 0;
@@ -97,65 +84,14 @@ cudaError_t launch_step(lbm_ctx* c, const void* fin, void* fout) {
   pd.s = c->s;
   pd.inv_s = 1.0 / c->s;
   const int coll = c->p.collision;
-    const void* tm = c->use_tma ? (const void*)&c->tmap[fin == c->buf[0] ? 0 : 1] : nullptr;
   switch (c->p.lattice) {
-    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st);
-    case LBM_D2V17: return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st);
+    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
+    case LBM_D2V17: return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
     case LBM_D2V37:
-      return c->p.thermal ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st)
-                          : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, tm, c->dev_err, c->st);
+      return c->p.thermal ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st)
+                          : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
   }
   return cudaErrorInvalidValue;
-}
-
-// Box of the TMA kernel that serves (lattice, storage) and the element size.
-template <class L>
-bool tma_box_l(int prec, int* boxw, int* boxh, int* esz) {
-  constexpr bool PAIR = L::Q <= 20;
-  switch (prec) {
-    case PREC_F32: *boxw = TmaCfg<L, float, PAIR>::BOXW; *boxh = TmaCfg<L, float, PAIR>::BY; *esz = 4; return true;
-    case PREC_F16: *boxw = TmaCfg<L, __half, PAIR>::BOXW; *boxh = TmaCfg<L, __half, PAIR>::BY; *esz = 2; return true;
-    case PREC_BF16:
-      *boxw = TmaCfg<L, __nv_bfloat16, PAIR>::BOXW; *boxh = TmaCfg<L, __nv_bfloat16, PAIR>::BY; *esz = 2; return true;
-    case PREC_I16: *boxw = TmaCfg<L, short, PAIR>::BOXW; *boxh = TmaCfg<L, short, PAIR>::BY; *esz = 2; return true;
-  }
-  return false;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-// Tensor maps [V][ny][pitch] of both population buffers for the TMA kernels; false leaves the
-// register-pull kernels in use.
-bool make_tensor_maps(lbm_ctx* c) {
-  if (!LBM_USE_TMA || c->p.thermal || c->prec == PREC_F64) return false;
-  int boxw = 0, boxh = 0, esz = 0;
-  bool ok = c->p.lattice == LBM_D2Q9    ? tma_box_l<D2Q9>(c->prec, &boxw, &boxh, &esz)
-            : c->p.lattice == LBM_D2V17 ? tma_box_l<D2V17>(c->prec, &boxw, &boxh, &esz)
-                                        : tma_box_l<D2V37>(c->prec, &boxw, &boxh, &esz);
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!ok || !enc) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)c->p.nx, (cuuint64_t)c->p.ny, (cuuint64_t)c->V};
-  const cuuint64_t strides[2] = {(cuuint64_t)c->g.pitch * esz, (cuuint64_t)c->g.plane * esz};
-  const cuuint32_t box[3] = {(cuuint32_t)boxw, (cuuint32_t)boxh, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  for (int b = 0; b < 2; ++b) {
-    if (enc(&c->tmap[b], dt, 3, c->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return false;
-  }
-  return true;
 }
 
 int ensure_scratch(lbm_ctx* c) {
@@ -259,9 +195,9 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
   c->s = s;
   c->elem = prec == PREC_F64 ? 8 : prec == PREC_F32 ? 4 : 2;  // the three 16-bit formats
   c->st = (cudaStream_t)p->stream;
-  const size_t row_bytes = ((size_t)p->nx * c->elem + 127) / 128 * 128 + LBM_ROW_PAD_BYTES;  // 128-byte lines
+  const size_t row_bytes = ((size_t)p->nx * c->elem + 127) / 128 * 128; // rows start on 128-byte lines
   c->g.pitch = (int)(row_bytes / c->elem);
-  c->g.plane = (long long)c->g.pitch * p->ny + LBM_PLANE_PAD_BYTES / (long long)c->elem;
+  c->g.plane = (long long)c->g.pitch * p->ny;
   c->g.nx = p->nx;
   c->g.ny = p->ny;
   c->g.bcx = p->bc_x;
@@ -288,7 +224,6 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     lbm_destroy(c);
     return LBM_ECUDA;
   }
-  c->use_tma = make_tensor_maps(c);
   *out = c;
   return LBM_OK;
 }

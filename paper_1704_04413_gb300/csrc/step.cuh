@@ -343,11 +343,11 @@ inline cudaError_t launch_step_lattice(int coll, int prec, const void* fin, void
 
 }  // namespace lbm
 
-// One translation unit per lattice instantiates its kernels behind these.  `tmap` (a CUtensorMap of
-// the input buffer) selects the TMA-staged kernels for the FP32 and 16-bit formats when not NULL.
+// One translation unit per lattice instantiates its kernels behind these.  `err` is the context's
+// device error word.
 #define LBM_STEP_LAUNCHER_ARGS                                                                      \
   int coll, int prec, const void *fin, void *fout, const lbm::StepGeom &g, const lbm::CollParamsD &pd, \
-      const void *tmap, int *err, cudaStream_t st
+      int *err, cudaStream_t st
 cudaError_t lbm_launch_step_d2q9(LBM_STEP_LAUNCHER_ARGS);
 cudaError_t lbm_launch_step_d2v17(LBM_STEP_LAUNCHER_ARGS);
 cudaError_t lbm_launch_step_d2v37(LBM_STEP_LAUNCHER_ARGS);

@@ -1,6 +1,7 @@
 // Stream-and-collide kernels of the D2V17 lattice (isothermal).
-#include "step_tma.cuh"
+#include "step.cuh"
 
 cudaError_t lbm_launch_step_d2v17(LBM_STEP_LAUNCHER_ARGS) {
-  return lbm::launch_step_any<lbm::D2V17, false>(coll, prec, fin, fout, g, pd, tmap, err, st);
+  (void)err;
+  return lbm::launch_step_lattice<lbm::D2V17, false>(coll, prec, fin, fout, g, pd, st);
 }
