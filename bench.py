@@ -261,6 +261,7 @@ def run_ours(args, rank, world, local_rank):
             lbm.lbm_destroy(ctx)
 
     accuracy = accuracy_vs_f64(st)
+    batched = batched_sweep_bench(stream_t, steps=max(10, min(args.steps, 200)))
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -272,11 +273,60 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
                              "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
-            "accuracy_vs_f64_gpu": accuracy,
+            "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(min_seconds=10.0)
         print(json.dumps(line), flush=True)
+
+
+def batched_sweep_bench(stream_t, steps, n=64, storage="f16"):
+    """64 shear-layer instances (sizes uniform over {128..1024}^2, Re log-uniform in [1e4, 1e6], D2Q9 / D2V17
+    alternating, shifted FP16 storage): autotuned persistent graph-captured batch vs one launch per instance."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    st = stream_t.cuda_stream
+    insts = wl.batched_sweep(n, seed=0)
+    ps, fields = [], []
+    for inst in insts:
+        V, cx, cy, w, cs2 = lbm.lbm_lattice_info(inst.lattice)
+        u0, nu, _ = wl.shear_layer_params(inst.L, np.sqrt(cs2), MACH, inst.reynolds)
+        ps.append(lbm.make_params(inst.lattice, inst.L, inst.L, nu=nu, collision="rr",
+                                  hermite_order=2 if inst.lattice == "D2Q9" else 3, storage=storage, stream=st))
+        fields.append(wl.double_shear_layer(inst.L, u0))
+    b = lbm.lbm_batch_create(ps)
+    try:
+        tune_ms = lbm.lbm_batch_autotune(b, 3)
+        ctxs = [lbm.lbm_batch_context(b, i) for i in range(n)]
+        for c, fl in zip(ctxs, fields):
+            lbm.lbm_init(c, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+        cells = sum(i.L * i.L for i in insts)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        lbm.lbm_batch_step(b, 4)
+        torch.cuda.synchronize()
+        e[0].record(stream_t)
+        lbm.lbm_batch_step(b, steps)
+        e[1].record(stream_t)
+        for c in ctxs:
+            lbm.lbm_step(c, 2)
+        torch.cuda.synchronize()
+        e[2].record(stream_t)
+        for _ in range(steps):
+            for c in ctxs:
+                lbm.lbm_step(c, 1)
+        e[3].record(stream_t)
+        torch.cuda.synchronize()
+        t_b, t_s = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+        t, r, q = lbm.lbm_batch_get_launch(b)
+        return {"instances": n, "cells": cells, "storage": storage, "collision": "rr",
+                "sizes": sorted({i.L for i in insts}), "steps": steps,
+                "launch": {"threads": t, "rows_per_item": r, "blocks_per_sm": q or "one block per item"},
+                "autotune_best_ms_per_step": round(tune_ms, 4),
+                "batched_glups": round(cells * steps / (t_b * 1e-3) / 1e9, 3),
+                "per_instance_launch_glups": round(cells * steps / (t_s * 1e-3) / 1e9, 3),
+                "speedup": round(t_s / t_b, 3)}
+    finally:
+        lbm.lbm_batch_destroy(b)
 
 
 def vorticity(ux, uy):
@@ -411,6 +461,7 @@ def main():
                     help="profiling case: run only this lattice's RR step (for ncu captures)")
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--storage", default="f32")
+    ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -422,6 +473,13 @@ def main():
         return
     if args.kernel_only:
         kernel_only(args)
+        return
+    if args.batched_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream_t = torch.cuda.Stream()
+        torch.cuda.set_stream(stream_t)
+        print(json.dumps(batched_sweep_bench(stream_t, steps=args.steps)))
         return
     if world > 1:
         import torch

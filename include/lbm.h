@@ -174,6 +174,47 @@ int lbm_load(lbm_ctx *c, const char *path);
 int lbm_conservation_noalloc(int lattice, int storage, const void *f, int nx, int ny, int pitch, double rho0,
                              double store_scale, double *out4, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched sweep: up to LBM_BATCH_MAX independent D2Q9 / D2V17 grids of any
+ * sizes and relaxation times, advanced together by one kernel launch per
+ * lattice per time step (one launch when all instances share a lattice; the
+ * launches recorded once in a CUDA graph and replayed).  Per cell the arithmetic is that of lbm_step, so a batched step
+ * is bit-identical to stepping each instance on its own.
+ * ------------------------------------------------------------------------ */
+#define LBM_BATCH_MAX 64
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+/* One context per entry of ps[0..n-1] (lattice D2Q9 or D2V17, isothermal,
+ * compute LBM_F32 with any non-FP64 storage; one collision model, one storage
+ * format and one stream for all).  Errors as lbm_create; LBM_EINVAL for
+ * n outside [1, LBM_BATCH_MAX] or mixed collision / storage / stream. */
+int lbm_batch_create(const lbm_params *ps, int n, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+
+/* The i-th instance's context, owned by the batch: use it with lbm_init,
+ * lbm_moments, lbm_conservation, ... (not lbm_destroy).  NULL if i is out of
+ * range.  Stepping an instance alone with lbm_step puts it out of phase with
+ * the others and makes lbm_batch_step return LBM_EINVAL. */
+lbm_ctx *lbm_batch_context(lbm_batch *b, int i);
+
+/* Advance every instance n >= 0 steps: graph replays of two steps each (the
+ * graph is recorded on first use) plus one direct launch for an odd n.
+ * Enqueued on the instances' stream; does not synchronize. */
+int lbm_batch_step(lbm_batch *b, int n);
+
+/* Launch shape of the batched kernel: threads per block (64, 128 or 256; each
+ * thread updates two neighbouring cells), rows per work item (1..64) and
+ * blocks per SM of a persistent grid (0 = one block per work item). */
+int lbm_batch_set_launch(lbm_batch *b, int threads, int rows, int blocks_per_sm);
+int lbm_batch_get_launch(const lbm_batch *b, int *threads, int *rows, int *blocks_per_sm);
+
+/* Autotuner: times every launch shape of the candidate set (threads
+ * {64,128,256} x rows {1,2,4,8} x blocks per SM {0 (one per item),2,4,8}) with 1 + `steps`
+ * batched steps each and keeps the fastest; *best_ms (may be NULL) receives its
+ * time per step.  Every timed step advances the instances, so tune before
+ * lbm_init (or re-initialise afterwards).  Synchronizes. */
+int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms);
+
 /* Text of a status code / of the context's last failure. */
 const char *lbm_strerror(int code);
 const char *lbm_last_error(const lbm_ctx *c);

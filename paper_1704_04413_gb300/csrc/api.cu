@@ -10,33 +10,13 @@
 #include <new>
 
 #include "../../include/lbm.h"
+#include "ctx.h"
 #include "fields.h"
 #include "step.cuh"
 
 
 using namespace lbm;
 
-struct lbm_ctx {
-  lbm_params p;
-  int V = 0;
-  int nmax = 0;
-  int prec = 0;   // PREC_*
-  int neq = 0, nreg = 0;
-  double cs2 = 0, tau = 0, rho0 = 1, s = 1;
-  size_t elem = 0;  // bytes per stored value
-  StepGeom g{};
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;
-  double* scratch = nullptr;  // 8 * ncells doubles, for host transfers and diagnostics
-  double* partials = nullptr;
-  double* out4 = nullptr;     // device: 4 sums, then the error word
-  double* host4 = nullptr;    // pinned host copy of the same
-  int* dev_err = nullptr;     // device error word (bounded device waits record LBM_ETIMEOUT there)
-  long long steps = 0;
-  cudaStream_t st = nullptr;
-  int device = 0;
-  char err[256] = {0};
-};
 
 namespace {
 
@@ -74,7 +54,9 @@ void lattice_copy(int* V, int* cx, int* cy, double* w, double* cs2) {
 
 int lattice_nmax(int lat) { return lat == LBM_D2V17 ? 3 : 4; }
 
-cudaError_t launch_step(lbm_ctx* c, const void* fin, void* fout) {
+}  // namespace
+
+cudaError_t lbm_ctx_launch_step(lbm_ctx* c, const void* fin, void* fout) {
   CollParamsD pd;
   pd.omega = 1.0 / c->tau;
   pd.om1 = 1.0 - 1.0 / c->tau;
@@ -93,6 +75,8 @@ cudaError_t launch_step(lbm_ctx* c, const void* fin, void* fout) {
   }
   return cudaErrorInvalidValue;
 }
+
+namespace {
 
 int ensure_scratch(lbm_ctx* c) {
   if (c->scratch) return LBM_OK;
@@ -269,7 +253,7 @@ int lbm_step(lbm_ctx* c, int n) {
   if (!c || n < 0) return fail(c, LBM_EINVAL, "lbm_step: n must be >= 0");
   LBM_CK(c, cudaSetDevice(c->device));
   for (int k = 0; k < n; ++k) {
-    LBM_CK(c, launch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]));
+    LBM_CK(c, lbm_ctx_launch_step(c, c->buf[c->cur], c->buf[c->cur ^ 1]));
     c->cur ^= 1;
   }
   c->steps += n;

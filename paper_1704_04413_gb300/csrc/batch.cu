@@ -1,0 +1,332 @@
+// Batched stream-and-collide: many independent grids (D2Q9 and D2V17, uneven
+// sizes and relaxation times) advanced by one launch per lattice per time step
+// (a single launch when all instances share a lattice), the launches captured
+// in a CUDA graph.
+//
+// Work item = `rows` consecutive rows x (2 * threads) columns of one
+// instance; items of all instances of a lattice are numbered consecutively and
+// either one block per item or a persistent grid of (SMs x blocks per SM)
+// blocks walks them.  The instance table travels
+// as a kernel parameter (constant bank); each item finds its instance by a
+// binary search over the first-item offsets.  Per cell the arithmetic is the
+// single-grid two-cell kernel's (step2_cells), so a batched step is bitwise
+// identical to per-instance lbm_step calls.
+//
+// The launch shape (threads per block, rows per item, blocks per SM) is chosen
+// by lbm_batch_autotune, which times every candidate on the batch itself.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "ctx.h"
+#include "step.cuh"
+
+namespace lbm {
+
+constexpr int kBatchMax = LBM_BATCH_MAX;
+
+struct BatchInst {
+  const void* fin;
+  void* fout;
+  StepGeom g;
+  CollParams<F2> P;
+  int ntx;         // items per row band
+  long long item0; // first work item of the instance
+};
+
+struct BatchDesc {
+  int n;
+  int rows;         // rows per work item
+  long long total;  // work items of all instances
+  BatchInst inst[kBatchMax];
+};
+
+template <class L, int COLL, class S>
+__global__ void __launch_bounds__(256, 1) k_batch(const __grid_constant__ BatchDesc d) {
+  for (long long it = blockIdx.x; it < d.total; it += gridDim.x) {
+    int lo = 0, hi = d.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (d.inst[mid].item0 <= it) lo = mid; else hi = mid - 1;
+    }
+    const BatchInst& I = d.inst[lo];
+    const long long local = it - I.item0;
+    const int band = (int)(local / I.ntx);
+    const int tx = (int)(local - (long long)band * I.ntx);
+    const int x = 2 * (tx * (int)blockDim.x + (int)threadIdx.x);
+    const int xw = 2 * (tx * (int)blockDim.x + (int)(threadIdx.x & ~31u));
+    if (x >= I.g.nx) continue;
+    const S* fin = static_cast<const S*>(I.fin);
+    S* fout = static_cast<S*>(I.fout);
+    for (int r = 0; r < d.rows; ++r) {
+      const int y = band * d.rows + r;
+      if (y >= I.g.ny) break;
+      GeomOffsets<L, S> off{I.g.plane * (long long)sizeof(S), (long long)I.g.pitch * (long long)sizeof(S)};
+      step2_cells<L, COLL, S>(fin, fout, I.g, I.P, off, x, y, xw);
+    }
+  }
+}
+
+// blocks_per_sm == 0: one block per work item; > 0: persistent grid of blocks_per_sm x SMs blocks.
+template <class L, int COLL, class S>
+cudaError_t batch_launch_t(const BatchDesc& d, int threads, int blocks_per_sm, int nsm, cudaStream_t st) {
+  if (d.n == 0 || d.total == 0) return cudaSuccess;
+  long long grid = blocks_per_sm > 0 ? (long long)blocks_per_sm * nsm : d.total;
+  if (grid > d.total) grid = d.total;
+  if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
+  k_batch<L, COLL, S><<<(unsigned)grid, threads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t batch_launch_s(int coll, const BatchDesc& d, int threads, int bps, int nsm, cudaStream_t st) {
+  switch (coll) {
+    case COLL_BGK: return batch_launch_t<L, COLL_BGK, S>(d, threads, bps, nsm, st);
+    case COLL_PR: return batch_launch_t<L, COLL_PR, S>(d, threads, bps, nsm, st);
+    case COLL_RR: return batch_launch_t<L, COLL_RR, S>(d, threads, bps, nsm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class L>
+cudaError_t batch_launch_l(int coll, int prec, const BatchDesc& d, int threads, int bps, int nsm, cudaStream_t st) {
+  switch (prec) {
+    case PREC_F32: return batch_launch_s<L, float>(coll, d, threads, bps, nsm, st);
+    case PREC_F16: return batch_launch_s<L, __half>(coll, d, threads, bps, nsm, st);
+    case PREC_BF16: return batch_launch_s<L, __nv_bfloat16>(coll, d, threads, bps, nsm, st);
+    case PREC_I16: return batch_launch_s<L, short>(coll, d, threads, bps, nsm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_batch {
+  int n = 0;
+  lbm_ctx* ctx[kBatchMax] = {nullptr};
+  int coll = 0, prec = 0;
+  int threads = 128, rows = 1, blocks_per_sm = 0;  // launch shape (0 = as many as fit)
+  cudaStream_t st = nullptr;       // the instances' stream
+  cudaStream_t capture = nullptr;  // private stream used to record the graph
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps, from parity 0 / 1 of the first instance
+  int nsm = 1;
+  int device = 0;
+};
+
+namespace {
+
+// Launch descriptor of the instances of one lattice, each reading buffer cur ^ flip.
+BatchDesc make_desc(const lbm_batch* b, int lattice, int flip) {
+  BatchDesc d{};
+  d.n = 0;
+  d.rows = b->rows;
+  long long item = 0;
+  for (int k = 0; k < b->n; ++k) {
+    const lbm_ctx* c = b->ctx[k];
+    if (c->p.lattice != lattice) continue;
+    BatchInst& I = d.inst[d.n++];
+    const int cur = c->cur ^ flip;
+    I.fin = c->buf[cur];
+    I.fout = c->buf[cur ^ 1];
+    I.g = c->g;
+    CollParamsD pd;
+    pd.omega = 1.0 / c->tau;
+    pd.om1 = 1.0 - 1.0 / c->tau;
+    pd.neq = c->neq;
+    pd.nreg = c->nreg;
+    pd.rho0 = c->rho0;
+    pd.s = c->s;
+    pd.inv_s = 1.0 / c->s;
+    I.P = cast_params<F2>(pd);
+    I.ntx = (c->p.nx + 2 * b->threads - 1) / (2 * b->threads);
+    I.item0 = item;
+    item += (long long)I.ntx * ((c->p.ny + b->rows - 1) / b->rows);
+  }
+  d.total = item;
+  return d;
+}
+
+// One batched time step: a launch per lattice present.
+cudaError_t batch_step_launch(const lbm_batch* b, int flip, cudaStream_t st) {
+  cudaError_t e = batch_launch_l<D2Q9>(b->coll, b->prec, make_desc(b, LBM_D2Q9, flip), b->threads, b->blocks_per_sm,
+                                       b->nsm, st);
+  if (e != cudaSuccess) return e;
+  return batch_launch_l<D2V17>(b->coll, b->prec, make_desc(b, LBM_D2V17, flip), b->threads, b->blocks_per_sm, b->nsm,
+                               st);
+}
+
+void drop_graphs(lbm_batch* b) {
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) {
+      cudaGraphExecDestroy(b->graph[k]);
+      b->graph[k] = nullptr;
+    }
+}
+
+// Two consecutive steps from the instances' current buffers, recorded on the private stream.
+cudaError_t build_graph(lbm_batch* b, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s)
+    e = batch_step_launch(b, s, b->capture);
+  cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+void advance(lbm_batch* b, int n) {
+  for (int k = 0; k < b->n; ++k) {
+    b->ctx[k]->cur ^= (n & 1);
+    b->ctx[k]->steps += n;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(const lbm_params* ps, int n, lbm_batch** out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!ps || n < 1 || n > kBatchMax) return LBM_EINVAL;
+  for (int k = 0; k < n; ++k) {
+    const lbm_params& p = ps[k];
+    if (p.lattice != LBM_D2Q9 && p.lattice != LBM_D2V17) return LBM_EINVAL;
+    if (p.thermal || p.compute != LBM_F32 || p.storage == LBM_F64) return LBM_EINVAL;
+    if (p.collision != ps[0].collision || p.storage != ps[0].storage || p.stream != ps[0].stream) return LBM_EINVAL;
+  }
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ENOMEM;
+  for (int k = 0; k < n; ++k) {
+    const int rc = lbm_create(&ps[k], &b->ctx[k]);
+    if (rc != LBM_OK) {
+      b->n = k;
+      lbm_batch_destroy(b);
+      return rc;
+    }
+  }
+  b->n = n;
+  b->coll = ps[0].collision;
+  b->prec = b->ctx[0]->prec;
+  b->st = static_cast<cudaStream_t>(ps[0].stream);
+  b->device = b->ctx[0]->device;
+  b->nsm = b->ctx[0]->g.nsm;
+  if (cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    lbm_batch_destroy(b);
+    return LBM_ECUDA;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  drop_graphs(b);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  for (int k = 0; k < b->n; ++k) lbm_destroy(b->ctx[k]);
+  delete b;
+}
+
+lbm_ctx* lbm_batch_context(lbm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->ctx[i];
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+  if (!b || n < 0) return LBM_EINVAL;
+  if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ECUDA;
+  // every instance must sit on the same buffer parity (it does unless one was stepped on its own)
+  const int par = b->ctx[0]->cur;
+  for (int k = 1; k < b->n; ++k)
+    if (b->ctx[k]->cur != par) return LBM_EINVAL;
+  int done = 0;
+  if (n >= 2) {
+    // one graph per buffer parity (all instances move together); each replay is two steps
+    if (!b->graph[par] && build_graph(b, &b->graph[par]) != cudaSuccess) return LBM_ECUDA;
+    for (; done + 2 <= n; done += 2)
+      if (cudaGraphLaunch(b->graph[par], b->st) != cudaSuccess) return LBM_ECUDA;
+  }
+  if (done < n) {
+    if (batch_step_launch(b, 0, b->st) != cudaSuccess) return LBM_ECUDA;
+  }
+  advance(b, n);
+  return LBM_OK;
+}
+
+int lbm_batch_set_launch(lbm_batch* b, int threads, int rows, int blocks_per_sm) {
+  if (!b || (threads != 64 && threads != 128 && threads != 256) || rows < 1 || rows > 64 || blocks_per_sm < 0)
+    return LBM_EINVAL;
+  b->threads = threads;
+  b->rows = rows;
+  b->blocks_per_sm = blocks_per_sm;
+  drop_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_get_launch(const lbm_batch* b, int* threads, int* rows, int* blocks_per_sm) {
+  if (!b) return LBM_EINVAL;
+  if (threads) *threads = b->threads;
+  if (rows) *rows = b->rows;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms) {
+  if (!b || steps < 1) return LBM_EINVAL;
+  if (cudaSetDevice(b->device) != cudaSuccess) return LBM_ECUDA;
+  const int threads_c[] = {64, 128, 256};
+  const int rows_c[] = {1, 2, 4, 8};
+  const int bps_c[] = {0, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LBM_ECUDA;
+  float best = 1e30f;
+  int bt = b->threads, br = b->rows, bb = b->blocks_per_sm;
+  int rc = LBM_OK;
+  for (int t : threads_c)
+    for (int r : rows_c)
+      for (int q : bps_c) {
+        b->threads = t;
+        b->rows = r;
+        b->blocks_per_sm = q;
+        // warm-up step, then `steps` timed steps (each one advances the instances)
+        bool ok = true;
+        for (int s = 0; s <= steps && ok; ++s) {
+          if (s == 1) ok = cudaEventRecord(e0, b->st) == cudaSuccess;
+          ok = ok && batch_step_launch(b, 0, b->st) == cudaSuccess;
+          if (ok) advance(b, 1);
+        }
+        ok = ok && cudaEventRecord(e1, b->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0;
+        ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (!ok) {
+          rc = LBM_ECUDA;
+          break;
+        }
+        ms /= steps;
+        if (ms < best) {
+          best = ms;
+          bt = t;
+          br = r;
+          bb = q;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->threads = bt;
+  b->rows = br;
+  b->blocks_per_sm = bb;
+  drop_graphs(b);
+  if (best_ms) *best_ms = best;
+  return rc;
+}
+
+}  // extern "C"

@@ -221,27 +221,46 @@ struct Step2Blocks {
   static constexpr int MIN = L::Q > 20 ? LBM_STEP2_MINB_LARGE : 1;
 };
 
-template <class L, int COLL, class S>
-__global__ void __launch_bounds__(STEP_BX, Step2Blocks<L>::MIN)
-    k_step2(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<F2> P,
-            const __grid_constant__ PullOffsets<L::Q> off) {
-  const int y = blockIdx.x / nbx;
-  const int bx = blockIdx.x - y * nbx;
-  const int x = 2 * (bx * STEP_BX + threadIdx.x);
-  if (x >= g.nx) return;
+// Offsets of the pulled source / the store of population i as template accessors: from the kernel
+// parameters (single-grid launches) or recomputed from the grid geometry (batched launches).
+template <int Q>
+struct ParamOffsets {
+  const PullOffsets<Q>& o;
+  template <int i>
+  __device__ __forceinline__ long long src() const { return o.src[i]; }
+  template <int i>
+  __device__ __forceinline__ long long dst() const { return o.dst[i]; }
+};
+template <class L, class S>
+struct GeomOffsets {
+  long long plane_b, pitch_b;  // bytes
+  template <int i>
+  __device__ __forceinline__ long long src() const {
+    constexpr int cx = L::CX[i], cy = L::CY[i];
+    return i * plane_b - cy * pitch_b - cx * (long long)sizeof(S);
+  }
+  template <int i>
+  __device__ __forceinline__ long long dst() const { return i * plane_b; }
+};
+
+// Two neighbouring cells (x, x+1) of row y: pull, collide, store.  xw is the first column of the
+// thread's warp (the interior test is uniform across the warp).
+template <class L, int COLL, class S, class OFF>
+__device__ __forceinline__ void step2_cells(const S* __restrict__ fin, S* __restrict__ fout, const StepGeom& g,
+                                            const CollParams<F2>& P, const OFF& off, int x, int y, int xw) {
   const bool two = x + 1 < g.nx;
-  const int xw = 2 * (bx * STEP_BX + (threadIdx.x & ~31));  // first column of the warp's 64
   const long long cen = (long long)y * g.pitch + x;
   F2 q[L::Q];
   if (xw >= L::VMAX && xw + 63 + L::VMAX < g.nx && y >= L::VMAX && y + L::VMAX < g.ny) {
     const char* c = reinterpret_cast<const char*>(fin + cen);
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
+      const long long so = off.template src<i>();
       if constexpr (L::CX[i] % 2 == 0) {
-        q[i] = ld_pair<S>(c + off.src[i]);
+        q[i] = ld_pair<S>(c + so);
       } else {
-        const float a = ld_raw<S>(c + off.src[i]);
-        const float b = ld_raw<S>(c + off.src[i] + (long long)sizeof(S));
+        const float a = ld_raw<S>(c + so);
+        const float b = ld_raw<S>(c + so + (long long)sizeof(S));
         q[i] = F2(a, b);
       }
     });
@@ -250,12 +269,13 @@ __global__ void __launch_bounds__(STEP_BX, Step2Blocks<L>::MIN)
     const int x1 = two ? x + 1 : x;  // a missing second cell repeats the first; it is not stored
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
-      const int ys = src_coord(y, L::CY[i], g.ny, g.bcy);
-      const int xs0 = src_coord(x, L::CX[i], g.nx, g.bcx);
-      const int xs1 = src_coord(x1, L::CX[i], g.nx, g.bcx);
+      constexpr int cx = L::CX[i], cy = L::CY[i];
+      const int ys = src_coord(y, cy, g.ny, g.bcy);
+      const int xs0 = src_coord(x, cx, g.nx, g.bcx);
+      const int xs1 = src_coord(x1, cx, g.nx, g.bcx);
       const long long row = (long long)ys * g.pitch;
-      const float a = ld_raw<S>(b + off.dst[i] + (row + xs0) * (long long)sizeof(S));
-      const float c = ld_raw<S>(b + off.dst[i] + (row + xs1) * (long long)sizeof(S));
+      const float a = ld_raw<S>(b + off.template dst<i>() + (row + xs0) * (long long)sizeof(S));
+      const float c = ld_raw<S>(b + off.template dst<i>() + (row + xs1) * (long long)sizeof(S));
       q[i] = F2(a, c);
     });
   }
@@ -264,14 +284,26 @@ __global__ void __launch_bounds__(STEP_BX, Step2Blocks<L>::MIN)
   if (two) {
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
-      st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), q[i]);
+      st_pair<S>(reinterpret_cast<S*>(o + off.template dst<i>()), q[i]);
     });
   } else {
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
-      Store<S>::st(reinterpret_cast<S*>(o + off.dst[i]), q[i].v.x);
+      Store<S>::st(reinterpret_cast<S*>(o + off.template dst<i>()), q[i].v.x);
     });
   }
+}
+
+template <class L, int COLL, class S>
+__global__ void __launch_bounds__(STEP_BX, Step2Blocks<L>::MIN)
+    k_step2(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<F2> P,
+            const __grid_constant__ PullOffsets<L::Q> off) {
+  const int y = blockIdx.x / nbx;
+  const int bx = blockIdx.x - y * nbx;
+  const int x = 2 * (bx * STEP_BX + threadIdx.x);
+  if (x >= g.nx) return;
+  const int xw = 2 * (bx * STEP_BX + (threadIdx.x & ~31));  // first column of the warp's 64
+  step2_cells<L, COLL, S>(fin, fout, g, P, ParamOffsets<L::Q>{off}, x, y, xw);
 }
 
 template <class L, int COLL, class S>

@@ -27,7 +27,8 @@ STORAGES = {"f64": F64, "f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT, "i16":
 EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_moments",
             "lbm_conservation", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
             "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error",
-            "lbm_conservation_noalloc"]
+            "lbm_conservation_noalloc", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_context",
+            "lbm_batch_step", "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_autotune"]
 
 
 class lbm_params(ctypes.Structure):
@@ -75,6 +76,13 @@ def load(path: str = LIB_PATH):
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_conservation_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int,
                                                     ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]),
+        "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(lbm_params), ctypes.c_int, ctypes.POINTER(vp)]),
+        "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_context": (vp, [vp, ctypes.c_int]),
+        "lbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lbm_batch_set_launch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "lbm_batch_get_launch": (ctypes.c_int, [vp, ip, ip, ip]),
+        "lbm_batch_autotune": (ctypes.c_int, [vp, ctypes.c_int, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -216,3 +224,41 @@ def lbm_conservation_noalloc(lattice, storage, f, nx, ny, pitch, out4, rho0=0.0,
     rc = load().lbm_conservation_noalloc(LATTICES.get(lattice, lattice), STORAGES.get(storage, storage), fp,
                                          nx, ny, pitch, rho0, store_scale, op, stream)
     return _check(rc, None, "lbm_conservation_noalloc")
+
+
+def lbm_batch_create(params_list):
+    arr = (lbm_params * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _check(load().lbm_batch_create(arr, len(params_list), ctypes.byref(b)), what="lbm_batch_create")
+    return b
+
+
+def lbm_batch_destroy(b) -> None:
+    load().lbm_batch_destroy(b)
+
+
+def lbm_batch_context(b, i: int):
+    p = load().lbm_batch_context(b, int(i))
+    if not p:
+        raise LbmError(EINVAL, "lbm_batch_context: index out of range")
+    return ctypes.c_void_p(p)
+
+
+def lbm_batch_step(b, n: int = 1):
+    return _check(load().lbm_batch_step(b, int(n)), what="lbm_batch_step")
+
+
+def lbm_batch_set_launch(b, threads: int, rows: int, blocks_per_sm: int):
+    return _check(load().lbm_batch_set_launch(b, threads, rows, blocks_per_sm), what="lbm_batch_set_launch")
+
+
+def lbm_batch_get_launch(b):
+    t, r, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().lbm_batch_get_launch(b, ctypes.byref(t), ctypes.byref(r), ctypes.byref(q)), what="lbm_batch_get_launch")
+    return t.value, r.value, q.value
+
+
+def lbm_batch_autotune(b, steps: int = 3) -> float:
+    ms = ctypes.c_double()
+    _check(load().lbm_batch_autotune(b, int(steps), ctypes.byref(ms)), what="lbm_batch_autotune")
+    return ms.value

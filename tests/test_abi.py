@@ -80,3 +80,16 @@ def test_invalid_parameters_are_rejected_on_host(lbm):
 def test_strerror(lbm):
     assert lbm.lbm_strerror(lbm.EINVAL) == "invalid argument"
     assert lbm.lbm_strerror(-99) == "unknown status"
+
+
+def test_batch_rejects_invalid_sets_on_host(lbm):
+    base = lbm.make_params("D2Q9", 32, 32, tau=0.7, storage="f16")
+    other = lbm.make_params("D2V17", 32, 32, tau=0.7, storage="f32")  # different storage
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_create([base, other])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_create([lbm.make_params("D2V37", 32, 32, tau=0.7, hermite_order=4, storage="f16")])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_create([base] * 65)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_create([lbm.make_params("D2Q9", 32, 32, tau=0.7, storage="f64")])

@@ -1,0 +1,103 @@
+"""Batched sweep (lbm_batch_*): one persistent graph-captured launch per step for many grids.
+
+The batched kernel runs the same per-cell arithmetic as lbm_step, so its result must be
+bit-identical to stepping every instance on its own (which is itself checked against the oracle in
+test_gpu_parity.py); the autotuner must leave that unchanged.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1704_04413_gb300 import workloads as wl
+
+from gpu_util import lib, stream
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [("D2Q9", 130, 70, 2e4), ("D2V17", 96, 64, 5e4), ("D2Q9", 300, 33, 1e5), ("D2V17", 257, 129, 3e4),
+          ("D2Q9", 64, 64, 1e4), ("D2V17", 190, 41, 1e6)]
+
+
+def params(m, storage):
+    out = []
+    for name, nx, ny, re in SHAPES:
+        cs2 = orc.lattice(name).cs2
+        u0, nu, _ = wl.shear_layer_params(nx, np.sqrt(cs2), 0.1, re)
+        out.append(m.make_params(name, nx, ny, nu=nu, collision="rr", hermite_order={"D2Q9": 2, "D2V17": 3}[name],
+                                 storage=storage, stream=stream()))
+    return out
+
+
+def init_all(m, ctxs):
+    for (name, nx, ny, re), c in zip(SHAPES, ctxs):
+        cs2 = orc.lattice(name).cs2
+        u0, _, _ = wl.shear_layer_params(nx, np.sqrt(cs2), 0.1, re)
+        fl = wl.double_shear_layer(nx, u0, ny=ny)
+        m.lbm_init(c, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+
+
+def pops(m, c, name, nx, ny):
+    V = orc.lattice(name).V
+    f = np.empty((V, ny, nx))
+    m.lbm_get_populations(c, f)
+    return f
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batched_steps_equal_single_steps_bitwise(storage):
+    m = lib()
+    ps = params(m, storage)
+    b = m.lbm_batch_create(ps)
+    singles = [m.lbm_create(p) for p in ps]
+    try:
+        bc = [m.lbm_batch_context(b, i) for i in range(len(ps))]
+        init_all(m, bc)
+        init_all(m, singles)
+        for n in (5, 2, 1):  # graph replays and a direct launch for the odd step
+            m.lbm_batch_step(b, n)
+            for c in singles:
+                m.lbm_step(c, n)
+        for (name, nx, ny, _), c0, c1 in zip(SHAPES, bc, singles):
+            assert m.lbm_step_count(c0) == m.lbm_step_count(c1) == 8
+            assert np.array_equal(pops(m, c0, name, nx, ny), pops(m, c1, name, nx, ny))
+    finally:
+        m.lbm_batch_destroy(b)
+        for c in singles:
+            m.lbm_destroy(c)
+
+
+def test_autotuned_launch_keeps_results():
+    m = lib()
+    ps = params(m, "f16")
+    b = m.lbm_batch_create(ps)
+    singles = [m.lbm_create(p) for p in ps]
+    try:
+        ms = m.lbm_batch_autotune(b, 2)
+        t, r, q = m.lbm_batch_get_launch(b)
+        assert ms > 0 and t in (64, 128, 256) and r in (1, 2, 4, 8) and q in (0, 2, 4, 8)
+        bc = [m.lbm_batch_context(b, i) for i in range(len(ps))]
+        init_all(m, bc)
+        init_all(m, singles)
+        m.lbm_batch_step(b, 6)
+        for c in singles:
+            m.lbm_step(c, 6)
+        for (name, nx, ny, _), c0, c1 in zip(SHAPES, bc, singles):
+            assert np.array_equal(pops(m, c0, name, nx, ny), pops(m, c1, name, nx, ny))
+    finally:
+        m.lbm_batch_destroy(b)
+        for c in singles:
+            m.lbm_destroy(c)
+
+
+def test_out_of_phase_instance_is_refused():
+    m = lib()
+    ps = params(m, "f32")[:2]
+    b = m.lbm_batch_create(ps)
+    try:
+        c0 = m.lbm_batch_context(b, 0)
+        m.lbm_step(c0, 1)
+        with pytest.raises(m.LbmError) as e:
+            m.lbm_batch_step(b, 2)
+        assert e.value.code == m.EINVAL
+    finally:
+        m.lbm_batch_destroy(b)
