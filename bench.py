@@ -262,6 +262,7 @@ def run_ours(args, rank, world, local_rank):
 
     accuracy = accuracy_vs_f64(st)
     batched = batched_sweep_bench(stream_t, steps=max(10, min(args.steps, 200)))
+    closure = closure_bench(stream_t, fine=2048, reynolds=1e6)
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -273,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
                              "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
-            "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
+            "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched, "learned_closure": closure,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(min_seconds=10.0)
@@ -327,6 +328,69 @@ def batched_sweep_bench(stream_t, steps, n=64, storage="f16"):
                 "speedup": round(t_s / t_b, 3)}
     finally:
         lbm.lbm_batch_destroy(b)
+
+
+def closure_bench(stream_t, fine=1024, factor=8, reynolds=1e5, seeds=4, epochs=20):
+    """Learned a1^(2) closure: training data from box-filtered fine D2Q9 RR shear layers, Adam training of the
+    BF16 tensor-core MLP, then the coarse grid run from the filtered initial state with and without the
+    closure, scored by the vorticity-spectrum error against the filtered fine run (lower is better)."""
+    import torch
+    from paper_1704_04413_gb300 import closure_pipeline as cp
+    from paper_1704_04413_gb300 import lbm
+    st = stream_t.cuda_stream
+    data = cp.generate(fine, factor, reynolds, seeds=range(seeds), stream=st)
+    cl, losses, train_s = cp.train(data, epochs=epochs)
+    try:
+        res = cp.compare(data, cl, stream=st)
+        # inference and closure-step throughput on 4M samples / the coarse grid
+        n = 1 << 22
+        x = data.x[torch.arange(n, device="cuda") % data.x.shape[0]].contiguous()
+        y = torch.empty((n, lbm.CLOSURE_OUT), dtype=torch.float32, device="cuda")
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(3):
+            lbm.lbm_closure_forward(cl, x, n, y, st)
+        e[0].record(stream_t)
+        for _ in range(10):
+            lbm.lbm_closure_forward(cl, x, n, y, st)
+        e[1].record(stream_t)
+        torch.cuda.synchronize()
+        fwd_ms = e[0].elapsed_time(e[1]) / 10
+        flops = 2 * (lbm.CLOSURE_IN * lbm.CLOSURE_HID + 2 * lbm.CLOSURE_HID ** 2 + lbm.CLOSURE_HID * lbm.CLOSURE_OUT)
+        nc = data.coarse
+        rates = {}
+        for mode in ("plain", "closure"):
+            c = lbm.lbm_create(lbm.make_params("D2Q9", nc, nc, nu=data.nu_coarse, collision="rr", hermite_order=2,
+                                               storage="f32", stream=st))
+            try:
+                fl = wl.double_shear_layer(nc, data.u0)
+                lbm.lbm_init(c, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+                step = (lambda k: lbm.lbm_step(c, k)) if mode == "plain" else \
+                    (lambda k: lbm.lbm_step_closure(c, cl, data.u0, k))
+                step(5)
+                e[0].record(stream_t)
+                step(200)
+                e[1].record(stream_t)
+                torch.cuda.synchronize()
+                rates[mode] = nc * nc * 200 / (e[0].elapsed_time(e[1]) * 1e-3) / 1e9
+            finally:
+                lbm.lbm_destroy(c)
+    finally:
+        lbm.lbm_closure_destroy(cl)
+    var = float(data.y[:, :3].var(dim=0).sum().item())
+    mean = lambda mode, key: round(float(np.mean([r[key] for r in res[mode]])), 4)
+    return {"fine": fine, "coarse": data.coarse, "reynolds": reynolds, "seeds": seeds,
+            "samples": int(data.x.shape[0]), "generate_s": round(data.seconds, 2),
+            "train": {"epochs": epochs, "batch": 4096, "seconds": round(train_s, 2),
+                      "samples_per_s": round(epochs * data.x.shape[0] / train_s, 0),
+                      "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "target_variance": var},
+            "forward": {"samples": n, "ms": round(fwd_ms, 4), "samples_per_s": round(n / (fwd_ms * 1e-3), 0),
+                        "tflops": round(flops * n / (fwd_ms * 1e-3) / 1e12, 2)},
+            "coarse_step_glups": {k: round(v, 3) for k, v in rates.items()},
+            "spectrum_err_mean": {"plain_rr": mean("plain", "spectrum_err"), "closure": mean("closure", "spectrum_err")},
+            "vorticity_rel_l2_mean": {"plain_rr": mean("plain", "vorticity_rel_l2"),
+                                      "closure": mean("closure", "vorticity_rel_l2")},
+            "per_snapshot": {m: [[r["coarse_step"], round(r["spectrum_err"], 3), round(r["vorticity_rel_l2"], 3)]
+                                 for r in res[m]] for m in res}}
 
 
 def vorticity(ux, uy):
@@ -462,6 +526,9 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
+    ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
+    ap.add_argument("--closure-fine", type=int, default=2048)
+    ap.add_argument("--closure-re", type=float, default=1e6)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -480,6 +547,13 @@ def main():
         stream_t = torch.cuda.Stream()
         torch.cuda.set_stream(stream_t)
         print(json.dumps(batched_sweep_bench(stream_t, steps=args.steps)))
+        return
+    if args.closure_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream_t = torch.cuda.Stream()
+        torch.cuda.set_stream(stream_t)
+        print(json.dumps(closure_bench(stream_t, fine=args.closure_fine, reynolds=args.closure_re)))
         return
     if world > 1:
         import torch

@@ -215,6 +215,53 @@ int lbm_batch_get_launch(const lbm_batch *b, int *threads, int *rows, int *block
  * lbm_init (or re-initialise afterwards).  Synchronizes. */
 int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms);
 
+/* ------------------------------------------------------------------------
+ * Learned closure for coarse grids (a per-cell MLP, not part of the paper's
+ * method: its fallback and the judge of its error is the plain RR step).
+ * Features of a cell: (rho - 1, ux, uy) / u0 of its 3x3 neighbourhood
+ * (periodic), 27 values padded to LBM_CLOSURE_IN, BF16 row-major.  Outputs:
+ * LBM_CLOSURE_OUT FP32 per cell, the first 3 being the subgrid stress
+ * (xx, xy, yy) / u0^2 that a box filter of a finer grid leaves out of the
+ * coarse equilibrium.  Network: IN -> HID -> HID -> HID -> OUT with GELU
+ * (tanh form) on the hidden layers; BF16 weights and activations, FP32
+ * accumulation (tensor-core MMA), FP32 master weights trained with Adam.
+ * Parameter layout (LBM_CLOSURE_NPARAM floats): W1[HID][IN] b1[HID]
+ * W2[HID][HID] b2[HID] W3[HID][HID] b3[HID] W4[OUT][HID] b4[OUT].
+ * Array pointers are device memory unless named *_host.
+ * ------------------------------------------------------------------------ */
+#define LBM_CLOSURE_IN 32
+#define LBM_CLOSURE_HID 64
+#define LBM_CLOSURE_OUT 8
+#define LBM_CLOSURE_NPARAM 10952
+typedef struct lbm_closure lbm_closure;
+
+/* Allocate a closure (weights zero, load them with lbm_closure_set_weights). */
+int lbm_closure_create(lbm_closure **out);
+void lbm_closure_destroy(lbm_closure *cl);
+/* Host FP32 parameters (n must be LBM_CLOSURE_NPARAM); setting resets the Adam state. */
+int lbm_closure_set_weights(lbm_closure *cl, const float *w_host, int n);
+int lbm_closure_get_weights(lbm_closure *cl, float *w_host, int n);
+/* y[n][OUT] = MLP(x[n][IN]) on `stream`. */
+int lbm_closure_forward(lbm_closure *cl, const void *x, int n, float *y, void *stream);
+/* One Adam step (lr, beta1 0.9, beta2 0.999) on the mean squared error of the 3 used outputs over
+ * the n samples (x, y_target[n][OUT]); *loss_host (may be NULL) receives the loss before the step. */
+int lbm_closure_train_step(lbm_closure *cl, const void *x, const float *y_target, int n, float lr,
+                           float *loss_host, void *stream);
+/* Gradient of that loss with respect to every parameter (host array of LBM_CLOSURE_NPARAM floats),
+ * without updating; synchronizes. */
+int lbm_closure_gradients(lbm_closure *cl, const void *x, const float *y_target, int n, float *grad_host,
+                          float *loss_host);
+/* Features of every cell of double fields rho, ux, uy [ny][nx] into x[nx*ny][IN]. */
+int lbm_closure_features(const double *rho, const double *ux, const double *uy, int nx, int ny, double u0,
+                         void *x, void *stream);
+/* Box filter by `factor` of fine fields [ny][nx] (both divisible by factor): coarse rho, u (density-
+ * weighted) into rho_c, ux_c, uy_c [ny/f][nx/f] and the subgrid stress / u0^2 into y[..][OUT]. */
+int lbm_closure_coarsen(const double *rho, const double *ux, const double *uy, int nx, int ny, int factor,
+                        double u0, double *rho_c, double *ux_c, double *uy_c, float *y, void *stream);
+/* n RR steps of a D2Q9 FP32 context whose a1^(2) gets the closure's correction
+ * Delta a1 = u0^2 y / (1 - 1/tau), y predicted each step from the current fields. */
+int lbm_step_closure(lbm_ctx *c, lbm_closure *cl, double u0, int n);
+
 /* Text of a status code / of the context's last failure. */
 const char *lbm_strerror(int code);
 const char *lbm_last_error(const lbm_ctx *c);

@@ -121,6 +121,7 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->partials);
   cudaFree(c->out4);
   cudaFree(c->dev_err);
+  cudaFree(c->closure_buf);
   cudaFreeHost(c->host4);
   delete c;
 }

@@ -222,8 +222,10 @@ __host__ __device__ constexpr double kappa(int a, int b) {
 // One collision.  q holds the pulled populations in storage representation
 // (converted to Real) and receives the post-collision ones.
 // ---------------------------------------------------------------------------
-template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real>
-__device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P) {
+// With CLOSURE, da[0..2] is added to the projected a1^(2) (xx, xy, yy) before the recursion (the
+// learned coarse-grid closure; closure.cu).
+template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real, bool CLOSURE = false>
+__device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P, const Real* da = nullptr) {
   using Sc = typename Scalar<Real>::type;
   static_assert(!(THERMAL && !__is_same(Sc, Real)), "the thermal path computes one cell per thread");
   constexpr double c2 = L::CS2;
@@ -334,6 +336,11 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
     B[2][0] = hmom(IC<2>{}, IC<0>{}) - A[2][0];
     B[1][1] = hmom(IC<1>{}, IC<1>{}) - A[1][1];
     B[0][2] = hmom(IC<0>{}, IC<2>{}) - A[0][2];
+    if constexpr (CLOSURE) {
+      B[2][0] += da[0];
+      B[1][1] += da[1];
+      B[0][2] += da[2];
+    }
     a1_third_from_second<L, THERMAL>(ux, uy, B);
     if constexpr (THERMAL && L::NMAX >= 3) {
       // App. C steps 2-4: projected a1^(3), averaged temperature-gradient terms, rebuilt a1^(3)

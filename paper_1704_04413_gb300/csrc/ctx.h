@@ -21,6 +21,7 @@ struct lbm_ctx {
   double* partials = nullptr;
   double* out4 = nullptr;     // device: 4 sums, then the error word
   double* host4 = nullptr;    // pinned host copy of the same
+  void* closure_buf = nullptr;  // features and outputs of the learned closure (lazily allocated)
   int* dev_err = nullptr;     // device error word (bounded device waits record LBM_ETIMEOUT there)
   long long steps = 0;
   cudaStream_t st = nullptr;

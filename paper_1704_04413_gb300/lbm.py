@@ -28,7 +28,10 @@ EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_st
             "lbm_conservation", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
             "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error",
             "lbm_conservation_noalloc", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_context",
-            "lbm_batch_step", "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_autotune"]
+            "lbm_batch_step", "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_autotune",
+            "lbm_closure_create", "lbm_closure_destroy", "lbm_closure_set_weights", "lbm_closure_get_weights",
+            "lbm_closure_forward", "lbm_closure_train_step", "lbm_closure_gradients", "lbm_closure_features",
+            "lbm_closure_coarsen", "lbm_step_closure"]
 
 
 class lbm_params(ctypes.Structure):
@@ -262,3 +265,111 @@ def lbm_batch_autotune(b, steps: int = 3) -> float:
     ms = ctypes.c_double()
     _check(load().lbm_batch_autotune(b, int(steps), ctypes.byref(ms)), what="lbm_batch_autotune")
     return ms.value
+
+
+# ---------------------------------------------------------------------------
+# Learned closure
+# ---------------------------------------------------------------------------
+CLOSURE_IN, CLOSURE_HID, CLOSURE_OUT, CLOSURE_NPARAM = 32, 64, 8, 10952
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_cuda or not a.is_contiguous():
+            raise TypeError("closure arrays must be contiguous CUDA tensors")
+        return a.data_ptr()
+    return int(a)
+
+
+def _closure_sigs(lib):
+    vp, fp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_double
+    sig = {
+        "lbm_closure_create": (ctypes.c_int, [ctypes.POINTER(vp)]),
+        "lbm_closure_destroy": (None, [vp]),
+        "lbm_closure_set_weights": (ctypes.c_int, [vp, fp, ctypes.c_int]),
+        "lbm_closure_get_weights": (ctypes.c_int, [vp, fp, ctypes.c_int]),
+        "lbm_closure_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp]),
+        "lbm_closure_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_float, fp, vp]),
+        "lbm_closure_gradients": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, fp, fp]),
+        "lbm_closure_features": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, dp, vp, vp]),
+        "lbm_closure_coarsen": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, vp, vp, vp,
+                                               vp, vp]),
+        "lbm_step_closure": (ctypes.c_int, [vp, vp, dp, ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+_closure_ready = False
+
+
+def _cl():
+    global _closure_ready
+    lib = load()
+    if not _closure_ready:
+        _closure_sigs(lib)
+        _closure_ready = True
+    return lib
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def lbm_closure_create():
+    c = ctypes.c_void_p()
+    _check(_cl().lbm_closure_create(ctypes.byref(c)), what="lbm_closure_create")
+    return c
+
+
+def lbm_closure_destroy(cl) -> None:
+    _cl().lbm_closure_destroy(cl)
+
+
+def lbm_closure_set_weights(cl, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    return _check(_cl().lbm_closure_set_weights(cl, _fptr(w), w.size), what="lbm_closure_set_weights")
+
+
+def lbm_closure_get_weights(cl) -> np.ndarray:
+    w = np.empty(CLOSURE_NPARAM, dtype=np.float32)
+    _check(_cl().lbm_closure_get_weights(cl, _fptr(w), w.size), what="lbm_closure_get_weights")
+    return w
+
+
+def lbm_closure_forward(cl, x, n, y, stream=None):
+    return _check(_cl().lbm_closure_forward(cl, _dptr(x), int(n), _dptr(y), stream), what="lbm_closure_forward")
+
+
+def lbm_closure_train_step(cl, x, y, n, lr, stream=None) -> float:
+    loss = np.zeros(1, dtype=np.float32)
+    _check(_cl().lbm_closure_train_step(cl, _dptr(x), _dptr(y), int(n), float(lr), _fptr(loss), stream),
+           what="lbm_closure_train_step")
+    return float(loss[0])
+
+
+def lbm_closure_gradients(cl, x, y, n):
+    g = np.empty(CLOSURE_NPARAM, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(_cl().lbm_closure_gradients(cl, _dptr(x), _dptr(y), int(n), _fptr(g), _fptr(loss)),
+           what="lbm_closure_gradients")
+    return g, float(loss[0])
+
+
+def lbm_closure_features(rho, ux, uy, nx, ny, u0, x, stream=None):
+    return _check(_cl().lbm_closure_features(_dptr(rho), _dptr(ux), _dptr(uy), nx, ny, float(u0), _dptr(x), stream),
+                  what="lbm_closure_features")
+
+
+def lbm_closure_coarsen(rho, ux, uy, nx, ny, factor, u0, rho_c, ux_c, uy_c, y, stream=None):
+    return _check(_cl().lbm_closure_coarsen(_dptr(rho), _dptr(ux), _dptr(uy), nx, ny, int(factor), float(u0),
+                                            _dptr(rho_c), _dptr(ux_c), _dptr(uy_c), _dptr(y), stream),
+                  what="lbm_closure_coarsen")
+
+
+def lbm_step_closure(ctx, cl, u0, n=1):
+    return _check(_cl().lbm_step_closure(ctx, cl, float(u0), int(n)), ctx, "lbm_step_closure")

@@ -131,3 +131,27 @@ def batched_sweep(n: int = 64, seed: int = 0, sizes=(128, 192, 256, 384, 512, 76
         re = float(math.exp(rng.uniform(math.log(re_range[0]), math.log(re_range[1]))))
         out.append(Instance(lattices[k % len(lattices)], L, re))
     return out
+
+
+def perturbed_shear_layer(L: int, u0: float, seed: int, kappa_range=(60.0, 100.0), delta_range=(0.03, 0.08)) -> Fields:
+    """Shear layer with a seeded perturbation amplitude delta and layer stiffness kappa."""
+    rng = np.random.default_rng(seed)
+    kappa = float(rng.uniform(*kappa_range))
+    delta = float(rng.uniform(*delta_range))
+    return double_shear_layer(L, u0, kappa=kappa, delta=delta)
+
+
+CLOSURE_LAYERS = [(64, 32), (64, 64), (64, 64), (8, 64)]  # (outputs, inputs) per layer
+
+
+def closure_initial_weights(seed: int, out_scale: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters of the closure network in its flat layout (W[out][in] then b[out] per
+    layer): He-normal hidden weights, the output layer scaled by out_scale, zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for k, (o, i) in enumerate(CLOSURE_LAYERS):
+        w = rng.normal(0.0, np.sqrt(2.0 / i), size=(o, i))
+        if k == len(CLOSURE_LAYERS) - 1:
+            w *= out_scale
+        parts += [w.ravel(), np.zeros(o)]
+    return np.concatenate(parts).astype(np.float32)
