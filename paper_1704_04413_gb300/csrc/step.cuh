@@ -126,15 +126,33 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
   const int bx = blockIdx.x - y * nbx;
   const int x = bx * STEP_BX + threadIdx.x;
   if (x >= g.nx) return;
-  // first column of this thread's warp: the interior test is uniform across the warp
-  const int xw = bx * STEP_BX + (threadIdx.x & ~31);
   const long long cen = (long long)y * g.pitch + x;
   Real q[L::Q];
-  if (xw >= L::VMAX && xw + 31 + L::VMAX < g.nx && y >= L::VMAX && y + L::VMAX < g.ny) {
+  // Rows at least VMAX away from the y edges (a block-uniform test): one load sequence for every
+  // column.  The x wrap (or clamp) enters as a per-thread base pointer for each x-velocity, moved
+  // by a whole row only where x - c_x leaves [0, nx); one fold suffices because nx >= VMAX.
+  // Keeping a single copy of the V loads matters: a second unrolled copy for edge columns,
+  // executed by a few warps per row, evicted the hot code from the instruction cache.
+  if (y >= L::VMAX && y + L::VMAX < g.ny && g.nx >= L::VMAX) {
     const char* c = reinterpret_cast<const char*>(fin + cen);
+    const char* cb[2 * L::VMAX + 1];
+    sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+      constexpr int cx = LBM_CI(J) - L::VMAX;
+      if constexpr (cx == 0) {
+        cb[LBM_CI(J)] = c;
+      } else {
+        const int xs = x - cx;
+        int fix;
+        if (g.bcx == BC_PERIODIC)
+          fix = (xs < 0 ? g.nx : 0) - (xs >= g.nx ? g.nx : 0);
+        else
+          fix = (xs < 0 ? -xs : 0) - (xs >= g.nx ? xs - g.nx + 1 : 0);
+        cb[LBM_CI(J)] = c + (long long)fix * (long long)sizeof(S);
+      }
+    });
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
-      q[i] = (Real)ld_raw<S>(c + off.src[i]);
+      q[i] = (Real)ld_raw<S>(cb[L::CX[i] + L::VMAX] + off.src[i]);
     });
   } else {
     const char* b = reinterpret_cast<const char*>(fin);
