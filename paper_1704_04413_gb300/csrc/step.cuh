@@ -269,16 +269,38 @@ __device__ __forceinline__ void step2_cells(const S* __restrict__ fin, S* __rest
   const bool two = x + 1 < g.nx;
   const long long cen = (long long)y * g.pitch + x;
   F2 q[L::Q];
-  if (xw >= L::VMAX && xw + 63 + L::VMAX < g.nx && y >= L::VMAX && y + L::VMAX < g.ny) {
+  // One load sequence for all rows VMAX away from the y edges, when either the warp's 64 columns
+  // need no x wrap or the x wrap is periodic on an even nx.  In the latter case both cells of a
+  // pair wrap together for an even c_x (x - c_x is even, so the 8-byte pair load stays aligned),
+  // and each cell gets its own base pointer for an odd c_x.  Base pointers move by a whole row only
+  // where x - c_x leaves [0, nx) (one fold: nx >= VMAX).
+  const bool x_inner = xw >= L::VMAX && xw + 63 + L::VMAX < g.nx;
+  const bool x_wrap_ok = g.bcx == BC_PERIODIC && (g.nx & 1) == 0 && g.nx >= L::VMAX;
+  if (y >= L::VMAX && y + L::VMAX < g.ny && (x_inner || x_wrap_ok)) {
     const char* c = reinterpret_cast<const char*>(fin + cen);
+    const char* cb0[2 * L::VMAX + 1];
+    const char* cb1[2 * L::VMAX + 1];
+    auto fold = [&](int xs) { return (xs < 0 ? g.nx : 0) - (xs >= g.nx ? g.nx : 0); };
+    sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+      constexpr int j = LBM_CI(J);
+      constexpr int cx = j - L::VMAX;
+      if constexpr (cx == 0) {
+        cb0[j] = c;
+        cb1[j] = c;
+      } else {
+        cb0[j] = c + (long long)fold(x - cx) * (long long)sizeof(S);
+        cb1[j] = (cx % 2 == 0) ? cb0[j] : c + (long long)fold(x + 1 - cx) * (long long)sizeof(S);
+      }
+    });
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
+      constexpr int j = L::CX[i] + L::VMAX;
       const long long so = off.template src<i>();
       if constexpr (L::CX[i] % 2 == 0) {
-        q[i] = ld_pair<S>(c + so);
+        q[i] = ld_pair<S>(cb0[j] + so);
       } else {
-        const float a = ld_raw<S>(c + so);
-        const float b = ld_raw<S>(c + so + (long long)sizeof(S));
+        const float a = ld_raw<S>(cb0[j] + so);
+        const float b = ld_raw<S>(cb1[j] + so + (long long)sizeof(S));
         q[i] = F2(a, b);
       }
     });
