@@ -222,6 +222,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                 "kernel": "k_step<D2V37,RR,isothermal,f32,f32> 1024^2", "algorithmic_bytes": dom_bytes,
                 "peak_source": peak_src + " hbm_gbs (copy)"}
+    sec = set(args.sections.split(","))
     # ---- e2e through the C ABI with host buffers (pinned), every step: init from host, step, moments to host ----
     h2d = d2h = 0
     hosts = []
@@ -229,7 +230,7 @@ def run_ours(args, rank, world, local_rank):
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hosts.append((ctx, pin(fl.rho), pin(fl.ux), pin(fl.uy), pin(fl.grad_u),
                       [torch.empty((GRID, GRID), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]))
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 5)) if "e2e" in sec else 0
     torch.cuda.synchronize()
     t_e = time.perf_counter()
     for _ in range(e2e_steps):
@@ -242,14 +243,15 @@ def run_ours(args, rank, world, local_rank):
     for _, r, u, v, g, outs in hosts:
         h2d += r.nbytes + u.nbytes + v.nbytes + g.nbytes
         d2h += sum(o.nbytes for o in outs)
-    e2e = {"value": round(len(ctxs) * ncell * e2e_steps / e2e_s / 1e9, 4), "unit": "GLUPS",
+    e2e = {"value": round(len(ctxs) * ncell * e2e_steps / max(e2e_s, 1e-9) / 1e9, 4), "unit": "GLUPS",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "path": "lbm_init(host rho,u,grad_u) + lbm_step(1) + lbm_moments(host) per lattice per step"}
     for _, _, ctx, _ in ctxs:
         lbm.lbm_destroy(ctx)
 
     # ---- low precision (shifted FP16 / BF16 storage) and FP64, same workload ----
-    for storage, k in (("f16", args.steps), ("bf16", args.steps), ("f64", max(2, min(args.steps // 10, 50)))):
+    other = (("f16", args.steps), ("bf16", args.steps), ("f64", max(2, min(args.steps // 10, 50))))
+    for storage, k in (other if "storages" in sec else ()):
         cs = make_contexts(storage, st)
         per_s, _, _ = timed_steps(cs, k, min(args.warmup, 2), stream_t)
         for (name, V, ctx, _), ms in zip(cs, per_s):
@@ -260,9 +262,9 @@ def run_ours(args, rank, world, local_rank):
                                           "vs_f32": round(glups / per_lattice[name]["f32"]["glups"], 3)}
             lbm.lbm_destroy(ctx)
 
-    accuracy = accuracy_vs_f64(st)
-    batched = batched_sweep_bench(stream_t, steps=max(10, min(args.steps, 200)))
-    closure = closure_bench(stream_t, fine=2048, reynolds=1e6)
+    accuracy = accuracy_vs_f64(st) if "accuracy" in sec else None
+    batched = batched_sweep_bench(stream_t, steps=max(10, min(args.steps, 200))) if "batched" in sec else None
+    closure = closure_bench(stream_t, fine=2048, reynolds=1e6) if "closure" in sec else None
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -277,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
             "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched, "learned_closure": closure,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(min_seconds=10.0)
+        line["cpu_baseline"] = cpu_baseline(min_seconds=10.0) if "cpu" in sec else None
         print(json.dumps(line), flush=True)
 
 
@@ -527,6 +529,9 @@ def main():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
+    ap.add_argument("--sections", default="e2e,storages,accuracy,batched,closure,cpu",
+                    help="comma list of sections run after the timed headline steps (profiling runs pass "
+                         "'none' to keep only the headline)")
     ap.add_argument("--closure-fine", type=int, default=2048)
     ap.add_argument("--closure-re", type=float, default=1e6)
     args = ap.parse_args()
