@@ -142,16 +142,16 @@ def shear_fields(name, L):
     return V, cs2, nu, wl.double_shear_layer(L, u0)
 
 
-def make_contexts(storage, stream):
+def make_contexts(storage, stream, grid=GRID):
     from paper_1704_04413_gb300 import lbm
     ctxs = []
     for name, neq in LATTICES:
-        V, cs2, nu, fl = shear_fields(name, GRID)
-        p = lbm.make_params(name, GRID, GRID, nu=nu, collision="rr", hermite_order=neq, storage=storage,
+        V, cs2, nu, fl = shear_fields(name, grid)
+        p = lbm.make_params(name, grid, grid, nu=nu, collision="rr", hermite_order=neq, storage=storage,
                             stream=stream)
         ctx = lbm.lbm_create(p)
         lbm.lbm_init(ctx, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
-        ctxs.append((name, V, ctx, fl))
+        ctxs.append((name, V, ctx, fl if grid == GRID else None))
     return ctxs
 
 
@@ -262,9 +262,24 @@ def run_ours(args, rank, world, local_rank):
                                           "vs_f32": round(glups / per_lattice[name]["f32"]["glups"], 3)}
             lbm.lbm_destroy(ctx)
 
+    # ---- above-L2 grids: consecutive steps of one 4096^2 grid (buffers 0.6-5 GB, far above the 129 MB L2) ----
+    large = {}
+    if "large" in sec:
+        for storage in ("f32", "f16", "bf16"):
+            for name, V, ctx, _ in make_contexts(storage, st, grid=4096):
+                per_s, _, _ = timed_steps([(name, V, ctx, None)], 20, 3, stream_t)
+                glups = 4096 * 4096 / (per_s[0] * 1e-3) / 1e9
+                gbs = glups * 2 * V * BYTES[storage]
+                large.setdefault(name, {})[storage] = {"glups": round(glups, 3), "gbs": round(gbs, 1),
+                                                       "frac": round(gbs / hbm_peak, 4)}
+                lbm.lbm_destroy(ctx)
+        for name in large:
+            for storage in ("f16", "bf16"):
+                large[name][storage]["vs_f32"] = round(large[name][storage]["glups"] / large[name]["f32"]["glups"], 3)
     accuracy = accuracy_vs_f64(st) if "accuracy" in sec else None
     batched = batched_sweep_bench(stream_t, steps=max(10, min(args.steps, 200))) if "batched" in sec else None
     closure = closure_bench(stream_t, fine=2048, reynolds=1e6) if "closure" in sec else None
+    stab = stability_bench(st) if "stability" in sec else None
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -276,7 +291,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
                              "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
-            "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched, "learned_closure": closure,
+            "per_lattice_4096": large, "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
+            "learned_closure": closure, "stability_map": stab,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(min_seconds=10.0) if "cpu" in sec else None
@@ -395,6 +411,21 @@ def closure_bench(stream_t, fine=1024, factor=8, reynolds=1e5, seeds=4, epochs=2
                                  for r in res[m]] for m in res}}
 
 
+def stability_bench(stream, reynolds=(1e4, 1e5, 1e6), L=128):
+    """M0^max of the double shear layer at L = 128 up to t = 2 t_c (Sec. III.B), FP32 storage, for BGK, the
+    projection at every order and the recursive regularization at every order >= 3, per lattice."""
+    from paper_1704_04413_gb300 import stability as S
+    t0 = time.perf_counter()
+    out = S.stability_map(reynolds=reynolds, L=L, stream=stream)
+    res = {"grid": L, "reynolds": list(reynolds), "criterion": "<u^2>(t) < <u^2>(0) for t <= 2 t_c, checked every 20 steps",
+           "storage": "f32", "dM0": 0.01}
+    for lat, d in out.items():
+        res[lat] = {k: ({"%g" % re: v[0] if isinstance(v, tuple) else v for re, v in d[k].items()}
+                        if isinstance(d[k], dict) else d[k]) for k in d}
+    res["seconds"] = round(time.perf_counter() - t0, 1)
+    return res
+
+
 def vorticity(ux, uy):
     """omega = d_x u_y - d_y u_x, fourth-order centred differences, periodic (Sec. III.B)."""
     def d(g, axis):
@@ -405,17 +436,25 @@ def vorticity(ux, uy):
 
 def accuracy_vs_f64(stream, L=256, storages=("f32", "f16", "bf16", "i16")):
     """Relative L2 error of vorticity (and of rho, u) after one convective time t_c = L/u0 of the
-    shear layer, each storage format against the FP64 GPU run of the same lattice."""
+    shear layer, each storage format against the FP64 GPU run of the same lattice.  "f64_perturbed" is a
+    control: the FP64 run with its initial populations multiplied by (1 + eta), eta uniform in
+    [-2^-24, 2^-24] (one FP32 rounding), i.e. the divergence the flow itself gives to rounding-size noise."""
     from paper_1704_04413_gb300 import lbm
     out = {}
     for name, neq in LATTICES:
         V, cs2, nu, fl = shear_fields(name, L)
         u0, _, steps = wl.shear_layer_params(L, np.sqrt(cs2), MACH, RE)
         res = {}
-        for storage in ("f64",) + tuple(storages):
-            p = lbm.make_params(name, L, L, nu=nu, collision="rr", hermite_order=neq, storage=storage, stream=stream)
+        for storage in ("f64",) + tuple(storages) + ("f64_perturbed",):
+            st_fmt = "f64" if storage == "f64_perturbed" else storage
+            p = lbm.make_params(name, L, L, nu=nu, collision="rr", hermite_order=neq, storage=st_fmt, stream=stream)
             ctx = lbm.lbm_create(p)
             lbm.lbm_init(ctx, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+            if storage == "f64_perturbed":
+                f = np.empty((V, L, L))
+                lbm.lbm_get_populations(ctx, f)
+                f *= 1.0 + wl.population_noise(V, L, L, seed=11, eps=2.0 ** -24)
+                lbm.lbm_set_populations(ctx, f)
             lbm.lbm_step(ctx, steps)
             r, u, v = (np.empty((L, L)) for _ in range(3))
             lbm.lbm_moments(ctx, r, u, v)
@@ -423,7 +462,7 @@ def accuracy_vs_f64(stream, L=256, storages=("f32", "f16", "bf16", "i16")):
             res[storage] = (r, u, v, vorticity(u, v))
         r0, u0_, v0, w0 = res["f64"]
         out[name] = {"steps": steps, "grid": L}
-        for storage in storages:
+        for storage in tuple(storages) + ("f64_perturbed",):
             r, u, v, w = res[storage]
             ok = bool(np.all(np.isfinite(w)))
             out[name][storage] = {
@@ -529,7 +568,7 @@ def main():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
-    ap.add_argument("--sections", default="e2e,storages,accuracy,batched,closure,cpu",
+    ap.add_argument("--sections", default="e2e,storages,large,accuracy,batched,closure,stability,cpu",
                     help="comma list of sections run after the timed headline steps (profiling runs pass "
                          "'none' to keep only the headline)")
     ap.add_argument("--closure-fine", type=int, default=2048)
