@@ -259,8 +259,16 @@ int lbm_closure_features(const double *rho, const double *ux, const double *uy, 
 int lbm_closure_coarsen(const double *rho, const double *ux, const double *uy, int nx, int ny, int factor,
                         double u0, double *rho_c, double *ux_c, double *uy_c, float *y, void *stream);
 /* n RR steps of a D2Q9 FP32 context whose a1^(2) gets the closure's correction
- * Delta a1 = u0^2 y / (1 - 1/tau), y predicted each step from the current fields. */
+ * Delta a1 = u0^2 y / (1 - 1/tau), y predicted each step from the current fields.  Two launches per
+ * step (the FP64 moments, then features + network + collision fused per tile of cells); the result is
+ * bitwise that of lbm_moments + lbm_closure_features + lbm_closure_forward + lbm_closure_apply.
+ * Allocates a work area of 96 B per cell on first use.  LBM_EINVAL unless the context is D2Q9, RR,
+ * isothermal, FP32 storage. */
 int lbm_step_closure(lbm_ctx *c, lbm_closure *cl, double u0, int n);
+/* One RR step of such a context with a caller-supplied correction field y[nx*ny][LBM_CLOSURE_OUT]
+ * (device, FP32; components 0..2 = xx, xy, yy of Delta a1 / u0^2 scaled as above), enqueued on the
+ * context's stream.  No counterpart in the paper: the entry point of a closure computed elsewhere. */
+int lbm_closure_apply(lbm_ctx *c, const float *y, double u0);
 
 /* Text of a status code / of the context's last failure. */
 const char *lbm_strerror(int code);

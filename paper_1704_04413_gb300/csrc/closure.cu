@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -39,17 +40,25 @@ constexpr int NPARAM = OFF_B4 + NO;
 static_assert(NPARAM == LBM_CLOSURE_NPARAM, "parameter count");
 
 // ---------------------------------------------------------------------------
-// GELU, tanh form (Hendrycks & Gimpel): 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+// GELU, tanh form (Hendrycks & Gimpel): 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).  tanh is the
+// hardware approximation (tanh.approx.f32, relative error about 2^-11): its error is below the BF16
+// rounding every activation gets next, and it keeps the layer chain short.  Training and inference use
+// the same function.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float tanh_hw(float u) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return t;
+}
 __device__ __forceinline__ float gelu(float z) {
   const float k = 0.7978845608028654f;
   const float u = k * (z + 0.044715f * z * z * z);
-  return 0.5f * z * (1.0f + tanhf(u));
+  return 0.5f * z * (1.0f + tanh_hw(u));
 }
 __device__ __forceinline__ float gelu_grad(float z) {
   const float k = 0.7978845608028654f;
   const float u = k * (z + 0.044715f * z * z * z);
-  const float t = tanhf(u);
+  const float t = tanh_hw(u);
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * z * z);
 }
 
@@ -89,24 +98,53 @@ __device__ __forceinline__ void mma_tile(float (&acc)[4], int m0, int n0, int K,
 }
 
 // BF16 weights in shared memory, [out][in] rows as in the parameter layout.
-struct SmemWeights {
+struct __align__(16) SmemWeights {
   __nv_bfloat16 w1[NH * NI], w2[NH * NH], w3[NH * NH], w4[NO * NH];
   float b1[NH], b2[NH], b3[NH], b4[NO];
 };
+static_assert(sizeof(SmemWeights) % 16 == 0, "whole 16-byte vectors");
+static_assert((OFF_W1 * 2) % 16 == 0 && (OFF_W2 * 2) % 16 == 0 && (OFF_W3 * 2) % 16 == 0 && (OFF_W4 * 2) % 16 == 0,
+              "BF16 weight blocks start on 16-byte boundaries");
+static_assert((OFF_B1 * 4) % 16 == 0 && (OFF_B2 * 4) % 16 == 0 && (OFF_B3 * 4) % 16 == 0 && (OFF_B4 * 4) % 16 == 0,
+              "FP32 bias blocks start on 16-byte boundaries");
 
+// Source of the j-th 16-byte vector of SmemWeights: the four BF16 weight blocks of the BF16 copy, then
+// the four FP32 bias blocks of the master weights (all 16-byte aligned: separate cudaMalloc buffers).
+__device__ __forceinline__ const uint4* weight_vec(int j, const __nv_bfloat16* wb, const float* wf) {
+  constexpr int E1 = NH * NI * 2 / 16, E2 = E1 + NH * NH * 2 / 16, E3 = E2 + NH * NH * 2 / 16,
+                E4 = E3 + NO * NH * 2 / 16, F1 = E4 + NH * 4 / 16, F2 = F1 + NH * 4 / 16, F3 = F2 + NH * 4 / 16;
+  const char* b = reinterpret_cast<const char*>(wb);
+  const char* f = reinterpret_cast<const char*>(wf);
+  if (j < E1) return reinterpret_cast<const uint4*>(b + OFF_W1 * 2) + j;
+  if (j < E2) return reinterpret_cast<const uint4*>(b + OFF_W2 * 2) + (j - E1);
+  if (j < E3) return reinterpret_cast<const uint4*>(b + OFF_W3 * 2) + (j - E2);
+  if (j < E4) return reinterpret_cast<const uint4*>(b + OFF_W4 * 2) + (j - E3);
+  if (j < F1) return reinterpret_cast<const uint4*>(f + OFF_B1 * 4) + (j - E4);
+  if (j < F2) return reinterpret_cast<const uint4*>(f + OFF_B2 * 4) + (j - F1);
+  if (j < F3) return reinterpret_cast<const uint4*>(f + OFF_B3 * 4) + (j - F2);
+  return reinterpret_cast<const uint4*>(f + OFF_B4 * 4) + (j - F3);
+}
+
+// Copy of the network into shared memory (the caller synchronizes the block afterwards).  Every thread
+// issues all its 16-byte loads before its first store, so the copy costs about one L2 round trip
+// instead of one per element.
 __device__ void load_weights(SmemWeights& s, const __nv_bfloat16* wb, const float* wf) {
-  for (int i = threadIdx.x; i < NH * NI; i += blockDim.x) s.w1[i] = wb[OFF_W1 + i];
-  for (int i = threadIdx.x; i < NH * NH; i += blockDim.x) {
-    s.w2[i] = wb[OFF_W2 + i];
-    s.w3[i] = wb[OFF_W3 + i];
+  constexpr int N16 = (int)(sizeof(SmemWeights) / 16);
+  constexpr int R = (N16 + 127) / 128;
+  uint4* dst = reinterpret_cast<uint4*>(&s);
+  for (int j0 = 0; j0 < N16; j0 += R * (int)blockDim.x) {
+    uint4 r[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int j = j0 + (int)threadIdx.x + k * (int)blockDim.x;
+      if (j < N16) r[k] = __ldg(weight_vec(j, wb, wf));
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int j = j0 + (int)threadIdx.x + k * (int)blockDim.x;
+      if (j < N16) dst[j] = r[k];
+    }
   }
-  for (int i = threadIdx.x; i < NO * NH; i += blockDim.x) s.w4[i] = wb[OFF_W4 + i];
-  for (int i = threadIdx.x; i < NH; i += blockDim.x) {
-    s.b1[i] = wf[OFF_B1 + i];
-    s.b2[i] = wf[OFF_B2 + i];
-    s.b3[i] = wf[OFF_B3 + i];
-  }
-  for (int i = threadIdx.x; i < NO; i += blockDim.x) s.b4[i] = wf[OFF_B4 + i];
 }
 
 // B fragments of a [out][in] weight matrix for the k-chunk k0 and output tile n0 (B[k][n] = W[n][k]).
@@ -117,36 +155,64 @@ __device__ __forceinline__ void wfrag(uint32_t (&rb)[2], const __nv_bfloat16* w,
   rb[1] = *reinterpret_cast<const uint32_t*>(row + 8);
 }
 
-// Hidden layer on register fragments: in a[KC][4] (K = 16 KC), out h as A fragments a_next[4][4] (K = 64).
+// Hidden layer on register fragments of two independent 16-row tiles: in a[2][KC][4] (K = 16 KC), out
+// GELU(a W^T + b) as the next layer's A fragments a_next[2][4][4] (K = 64).  Each weight fragment is read
+// once for both tiles and the two MMA chains overlap.
 template <int KC>
-__device__ __forceinline__ void dense_gelu(const uint32_t (&a)[KC][4], const __nv_bfloat16* w, const float* b,
-                                           uint32_t (&a_next)[4][4]) {
+__device__ __forceinline__ void dense_gelu2(const uint32_t (&a)[2][KC][4], const __nv_bfloat16* w, const float* b,
+                                            uint32_t (&a_next)[2][4][4]) {
   const int lane = threadIdx.x & 31, t = lane & 3;
-  float acc[8][4];
+  float acc[2][8][4];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const float b0 = b[j * 8 + 2 * t], b1 = b[j * 8 + 2 * t + 1];
-    acc[j][0] = b0;
-    acc[j][1] = b1;
-    acc[j][2] = b0;
-    acc[j][3] = b1;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      acc[h][j][0] = b0;
+      acc[h][j][1] = b1;
+      acc[h][j][2] = b0;
+      acc[h][j][3] = b1;
+    }
 #pragma unroll
     for (int kc = 0; kc < KC; ++kc) {
       uint32_t rb[2];
       wfrag(rb, w, 16 * KC, kc * 16, j * 8);
-      mma16816(acc[j], a[kc], rb);
+      mma16816(acc[0][j], a[0][kc], rb);
+      mma16816(acc[1][j], a[1][kc], rb);
     }
   }
 #pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      a_next[h][kc][0] = pack_bf16(gelu(acc[h][2 * kc][0]), gelu(acc[h][2 * kc][1]));
+      a_next[h][kc][1] = pack_bf16(gelu(acc[h][2 * kc][2]), gelu(acc[h][2 * kc][3]));
+      a_next[h][kc][2] = pack_bf16(gelu(acc[h][2 * kc + 1][0]), gelu(acc[h][2 * kc + 1][1]));
+      a_next[h][kc][3] = pack_bf16(gelu(acc[h][2 * kc + 1][2]), gelu(acc[h][2 * kc + 1][3]));
+    }
+}
+
+// Output layer (8 columns, no activation) on two tiles: o[h] = b4 + h3[h] W4^T.
+__device__ __forceinline__ void dense_out2(const uint32_t (&a)[2][4][4], const __nv_bfloat16* w, const float* b,
+                                           float (&o)[2][4]) {
+  const int t = threadIdx.x & 3;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    o[h][0] = b[2 * t];
+    o[h][1] = b[2 * t + 1];
+    o[h][2] = b[2 * t];
+    o[h][3] = b[2 * t + 1];
+  }
+#pragma unroll
   for (int kc = 0; kc < 4; ++kc) {
-    a_next[kc][0] = pack_bf16(gelu(acc[2 * kc][0]), gelu(acc[2 * kc][1]));
-    a_next[kc][1] = pack_bf16(gelu(acc[2 * kc][2]), gelu(acc[2 * kc][3]));
-    a_next[kc][2] = pack_bf16(gelu(acc[2 * kc + 1][0]), gelu(acc[2 * kc + 1][1]));
-    a_next[kc][3] = pack_bf16(gelu(acc[2 * kc + 1][2]), gelu(acc[2 * kc + 1][3]));
+    uint32_t rb[2];
+    wfrag(rb, w, NH, kc * 16, 0);
+    mma16816(o[0], a[0][kc], rb);
+    mma16816(o[1], a[1][kc], rb);
   }
 }
 
-// Inference: y[n][NO] (FP32) for x[n][NI] (BF16); each warp takes 16 rows at a time.
+// Inference: y[n][NO] (FP32) for x[n][NI] (BF16); each warp takes 32 rows (two 16-row tiles) at a time.
 __global__ void __launch_bounds__(128) k_mlp_forward(const __nv_bfloat16* __restrict__ x, int n,
                                                      const __nv_bfloat16* __restrict__ wb,
                                                      const float* __restrict__ wf, float* __restrict__ y) {
@@ -155,36 +221,38 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const __nv_bfloat16* __rest
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (long long r0 = ((long long)blockIdx.x * nwarps + warp) * 16; r0 < n;
-       r0 += (long long)gridDim.x * nwarps * 16) {
-    uint32_t a0[2][4];
-    const long long ra = r0 + g, rbr = r0 + g + 8;
+  for (long long r0 = ((long long)blockIdx.x * nwarps + warp) * 32; r0 < n;
+       r0 += (long long)gridDim.x * nwarps * 32) {
+    uint32_t a0[2][2][4];
 #pragma unroll
-    for (int kc = 0; kc < 2; ++kc) {
-      const int c = kc * 16 + 2 * t;
-      a0[kc][0] = ra < n ? *reinterpret_cast<const uint32_t*>(x + ra * NI + c) : 0u;
-      a0[kc][1] = rbr < n ? *reinterpret_cast<const uint32_t*>(x + rbr * NI + c) : 0u;
-      a0[kc][2] = ra < n ? *reinterpret_cast<const uint32_t*>(x + ra * NI + c + 8) : 0u;
-      a0[kc][3] = rbr < n ? *reinterpret_cast<const uint32_t*>(x + rbr * NI + c + 8) : 0u;
-    }
-    uint32_t h1[4][4], h2[4][4], h3[4][4];
-    dense_gelu<2>(a0, s.w1, s.b1, h1);
-    dense_gelu<4>(h1, s.w2, s.b2, h2);
-    dense_gelu<4>(h2, s.w3, s.b3, h3);
-    float o[4] = {s.b4[2 * t], s.b4[2 * t + 1], s.b4[2 * t], s.b4[2 * t + 1]};
+    for (int h = 0; h < 2; ++h) {
+      const long long ra = r0 + 16 * h + g, rbr = ra + 8;
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-      uint32_t rb[2];
-      wfrag(rb, s.w4, NH, kc * 16, 0);
-      mma16816(o, h3[kc], rb);
+      for (int kc = 0; kc < 2; ++kc) {
+        const int c = kc * 16 + 2 * t;
+        a0[h][kc][0] = ra < n ? *reinterpret_cast<const uint32_t*>(x + ra * NI + c) : 0u;
+        a0[h][kc][1] = rbr < n ? *reinterpret_cast<const uint32_t*>(x + rbr * NI + c) : 0u;
+        a0[h][kc][2] = ra < n ? *reinterpret_cast<const uint32_t*>(x + ra * NI + c + 8) : 0u;
+        a0[h][kc][3] = rbr < n ? *reinterpret_cast<const uint32_t*>(x + rbr * NI + c + 8) : 0u;
+      }
     }
-    if (ra < n) {
-      y[ra * NO + 2 * t] = o[0];
-      y[ra * NO + 2 * t + 1] = o[1];
-    }
-    if (rbr < n) {
-      y[rbr * NO + 2 * t] = o[2];
-      y[rbr * NO + 2 * t + 1] = o[3];
+    uint32_t h1[2][4][4], h2[2][4][4], h3[2][4][4];
+    dense_gelu2<2>(a0, s.w1, s.b1, h1);
+    dense_gelu2<4>(h1, s.w2, s.b2, h2);
+    dense_gelu2<4>(h2, s.w3, s.b3, h3);
+    float o[2][4];
+    dense_out2(h3, s.w4, s.b4, o);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long ra = r0 + 16 * h + g, rbr = ra + 8;
+      if (ra < n) {
+        y[ra * NO + 2 * t] = o[h][0];
+        y[ra * NO + 2 * t + 1] = o[h][1];
+      }
+      if (rbr < n) {
+        y[rbr * NO + 2 * t] = o[h][2];
+        y[rbr * NO + 2 * t + 1] = o[h][3];
+      }
     }
   }
 }
@@ -458,6 +526,109 @@ __global__ void __launch_bounds__(128) k_step_closure(const float* __restrict__ 
   });
 }
 
+// ---------------------------------------------------------------------------
+// Fused closure step: features, MLP and the corrected collision of a 32 x 4 tile of cells per block
+// iteration (warp w takes row w of the tile, one cell per lane).  The moments of the tile and its
+// one-cell halo (periodic, as lbm_closure_features) are converted to BF16 features in shared memory
+// once; each warp builds its two 16-cell A fragments from them, runs the layer chain of
+// k_mlp_forward, leaves the three used outputs of its 32 cells in shared memory and then pulls,
+// collides and stores its cells as k_step_closure does.  Same arithmetic in the same order as
+// features + forward + k_step_closure, so the result is bitwise the three-kernel path's.
+// ---------------------------------------------------------------------------
+constexpr int FT_X = 32, FT_Y = 4;
+
+struct SmemFused {
+  SmemWeights w;
+  __nv_bfloat16 m[FT_Y + 2][FT_X + 2][3];  // (rho - 1, ux, uy) / u0 of the tile and its halo
+  float y[FT_Y][FT_X][3];
+};
+
+__global__ void __launch_bounds__(128) k_step_closure_fused(const float* __restrict__ fin, float* __restrict__ fout,
+                                                            lbm::StepGeom g, lbm::CollParams<float> P,
+                                                            const double* __restrict__ rho,
+                                                            const double* __restrict__ ux,
+                                                            const double* __restrict__ uy, double inv_u0,
+                                                            const __nv_bfloat16* __restrict__ wb,
+                                                            const float* __restrict__ wf, float scale) {
+  using L = lbm::D2Q9;
+  __shared__ SmemFused s;
+  load_weights(s.w, wb, wf);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, t = lane & 3;
+  const int tiles_x = (g.nx + FT_X - 1) / FT_X, tiles_y = (g.ny + FT_Y - 1) / FT_Y;
+  for (long long tile = blockIdx.x; tile < (long long)tiles_x * tiles_y; tile += gridDim.x) {
+    const int x0 = (int)(tile % tiles_x) * FT_X, y0 = (int)(tile / tiles_x) * FT_Y;
+    __syncthreads();  // previous tile's features and outputs are no longer read
+    for (int k = threadIdx.x; k < (FT_Y + 2) * (FT_X + 2); k += blockDim.x) {
+      const int hy = k / (FT_X + 2), hx = k - hy * (FT_X + 2);
+      int xs = (x0 + hx - 1) % g.nx, ys = (y0 + hy - 1) % g.ny;
+      if (xs < 0) xs += g.nx;
+      if (ys < 0) ys += g.ny;
+      const long long c = (long long)ys * g.nx + xs;
+      s.m[hy][hx][0] = __float2bfloat16((float)((rho[c] - 1.0) * inv_u0));
+      s.m[hy][hx][1] = __float2bfloat16((float)(ux[c] * inv_u0));
+      s.m[hy][hx][2] = __float2bfloat16((float)(uy[c] * inv_u0));
+    }
+    __syncthreads();
+    // feature k of the cell in column cx of this warp's row: neighbour k / 3 (row-major over the 3 x 3
+    // stencil), component k % 3; zero beyond the 27 used inputs
+    auto feat = [&](int cx, int k) -> __nv_bfloat16 {
+      if (k >= 27) return __float2bfloat16(0.0f);
+      const int j = k / 3;
+      return s.m[warp + j / 3][cx + j % 3][k - 3 * j];
+    };
+    uint32_t a0[2][2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ra = h * 16 + gq, rb = ra + 8;
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc) {
+        const int c = kc * 16 + 2 * t;
+        a0[h][kc][0] = pack_raw(feat(ra, c), feat(ra, c + 1));
+        a0[h][kc][1] = pack_raw(feat(rb, c), feat(rb, c + 1));
+        a0[h][kc][2] = pack_raw(feat(ra, c + 8), feat(ra, c + 9));
+        a0[h][kc][3] = pack_raw(feat(rb, c + 8), feat(rb, c + 9));
+      }
+    }
+    uint32_t h1[2][4][4], h2[2][4][4], h3[2][4][4];
+    dense_gelu2<2>(a0, s.w.w1, s.w.b1, h1);
+    dense_gelu2<4>(h1, s.w.w2, s.w.b2, h2);
+    dense_gelu2<4>(h2, s.w.w3, s.w.b3, h3);
+    float o[2][4];
+    dense_out2(h3, s.w.w4, s.w.b4, o);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ra = h * 16 + gq, rb = ra + 8;
+      if (t == 0) {
+        s.y[warp][ra][0] = o[h][0];
+        s.y[warp][ra][1] = o[h][1];
+        s.y[warp][rb][0] = o[h][2];
+        s.y[warp][rb][1] = o[h][3];
+      } else if (t == 1) {
+        s.y[warp][ra][2] = o[h][0];
+        s.y[warp][rb][2] = o[h][2];
+      }
+    }
+    __syncwarp();
+    const int x = x0 + lane, yy = y0 + warp;
+    if (x < g.nx && yy < g.ny) {
+      float q[L::Q];
+      lbm::sfor<0, L::Q>([&](auto I) {
+        constexpr int i = LBM_CI(I);
+        constexpr int cx = L::CX[i], cy = L::CY[i];
+        const int xs = lbm::src_coord(x, cx, g.nx, g.bcx);
+        const int ys = lbm::src_coord(yy, cy, g.ny, g.bcy);
+        q[i] = fin[(long long)i * g.plane + (long long)ys * g.pitch + xs];
+      });
+      const float da[3] = {scale * s.y[warp][lane][0], scale * s.y[warp][lane][1], scale * s.y[warp][lane][2]};
+      lbm::collide<L, lbm::COLL_RR, false, false, float, true>(q, P, da);
+      lbm::sfor<0, L::Q>([&](auto I) {
+        constexpr int i = LBM_CI(I);
+        fout[(long long)i * g.plane + (long long)yy * g.pitch + x] = q[i];
+      });
+    }
+  }
+}
+
 struct lbm_closure {
   float* w = nullptr;            // FP32 master weights
   __nv_bfloat16* wb = nullptr;   // BF16 copy
@@ -534,8 +705,8 @@ int lbm_closure_forward(lbm_closure* c, const void* x, int n, float* y, void* st
   if (!c || !x || !y || n < 0) return LBM_EINVAL;
   if (n == 0) return LBM_OK;
   cudaSetDevice(c->device);
-  const long long tiles = ((long long)n + 15) / 16;
-  long long blocks = (tiles + 3) / 4;
+  const long long pairs = ((long long)n + 31) / 32;  // 32 rows per warp iteration
+  long long blocks = (pairs + 3) / 4;
   if (blocks > 4096) blocks = 4096;
   k_mlp_forward<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)x, n, c->wb, c->w, y);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
@@ -588,22 +759,11 @@ int lbm_closure_train_step(lbm_closure* c, const void* x, const float* y, int n,
   return LBM_OK;
 }
 
-int lbm_step_closure(lbm_ctx* c, lbm_closure* cl, double u0, int n) {
-  if (!c || !cl || n < 0 || !(u0 > 0)) return LBM_EINVAL;
-  if (c->p.lattice != LBM_D2Q9 || c->p.collision != LBM_RR || c->prec != lbm::PREC_F32 || c->p.thermal)
-    return LBM_EINVAL;
-  if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ECUDA;
-  const long long cells = (long long)c->p.nx * c->p.ny;
-  if (!c->closure_buf) {
-    // rho, ux, uy (double) | features (BF16) | outputs (FP32)
-    const size_t bytes = cells * (3 * sizeof(double) + NI * sizeof(__nv_bfloat16) + NO * sizeof(float));
-    if (cudaMalloc(&c->closure_buf, bytes) != cudaSuccess) return LBM_ENOMEM;
-  }
-  double* r = static_cast<double*>(c->closure_buf);
-  double* u = r + cells;
-  double* v = u + cells;
-  __nv_bfloat16* feat = reinterpret_cast<__nv_bfloat16*>(v + cells);
-  float* y = reinterpret_cast<float*>(feat + cells * NI);
+static bool closure_ctx_ok(const lbm_ctx* c) {
+  return c->p.lattice == LBM_D2Q9 && c->p.collision == LBM_RR && c->prec == lbm::PREC_F32 && !c->p.thermal;
+}
+
+static lbm::CollParams<float> closure_coll_params(const lbm_ctx* c) {
   lbm::CollParamsD pd;
   pd.omega = 1.0 / c->tau;
   pd.om1 = 1.0 - 1.0 / c->tau;
@@ -612,16 +772,52 @@ int lbm_step_closure(lbm_ctx* c, lbm_closure* cl, double u0, int n) {
   pd.rho0 = c->rho0;
   pd.s = c->s;
   pd.inv_s = 1.0 / c->s;
-  const lbm::CollParams<float> P = lbm::cast_params<float>(pd);
+  return lbm::cast_params<float>(pd);
+}
+
+int lbm_closure_apply(lbm_ctx* c, const float* y, double u0) {
+  if (!c || !y || !(u0 > 0)) return LBM_EINVAL;
+  if (!closure_ctx_ok(c)) return LBM_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ECUDA;
+  const long long cells = (long long)c->p.nx * c->p.ny;
   // the correction Delta a1 enters the post-collision flux as (1 - 1/tau) Delta a1 = tau_sgs
   const float scale = (float)(u0 * u0 / (1.0 - 1.0 / c->tau));
-  const unsigned blocks = (unsigned)((cells + 127) / 128);
+  k_step_closure<<<(unsigned)((cells + 127) / 128), 128, 0, c->st>>>(
+      static_cast<const float*>(c->buf[c->cur]), static_cast<float*>(c->buf[c->cur ^ 1]), c->g,
+      closure_coll_params(c), y, scale);
+  if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+  c->cur ^= 1;
+  c->steps += 1;
+  return LBM_OK;
+}
+
+int lbm_step_closure(lbm_ctx* c, lbm_closure* cl, double u0, int n) {
+  if (!c || !cl || n < 0 || !(u0 > 0)) return LBM_EINVAL;
+  if (!closure_ctx_ok(c)) return LBM_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ECUDA;
+  const long long cells = (long long)c->p.nx * c->p.ny;
+  if (!c->closure_buf) {
+    // rho, ux, uy (double) | features (BF16) | outputs (FP32): the fused step uses the first part,
+    // the rest serves callers composing the stages themselves
+    const size_t bytes = cells * (3 * sizeof(double) + NI * sizeof(__nv_bfloat16) + NO * sizeof(float));
+    if (cudaMalloc(&c->closure_buf, bytes) != cudaSuccess) return LBM_ENOMEM;
+  }
+  double* r = static_cast<double*>(c->closure_buf);
+  double* u = r + cells;
+  double* v = u + cells;
+  const lbm::CollParams<float> P = closure_coll_params(c);
+  const float scale = (float)(u0 * u0 / (1.0 - 1.0 / c->tau));
+  const long long tiles = (long long)((c->p.nx + FT_X - 1) / FT_X) * ((c->p.ny + FT_Y - 1) / FT_Y);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_closure_fused, 128, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const long long grid = std::min<long long>(tiles, (long long)per_sm * c->g.nsm);
   for (int k = 0; k < n; ++k) {
     if (lbm_moments(c, r, u, v, nullptr, 1) != LBM_OK) return LBM_ECUDA;
-    k_features<<<(unsigned)((cells + 255) / 256), 256, 0, c->st>>>(r, u, v, c->p.nx, c->p.ny, 1.0 / u0, feat);
-    if (lbm_closure_forward(cl, feat, (int)cells, y, c->st) != LBM_OK) return LBM_ECUDA;
-    k_step_closure<<<blocks, 128, 0, c->st>>>(static_cast<const float*>(c->buf[c->cur]),
-                                             static_cast<float*>(c->buf[c->cur ^ 1]), c->g, P, y, scale);
+    k_step_closure_fused<<<(unsigned)grid, 128, 0, c->st>>>(
+        static_cast<const float*>(c->buf[c->cur]), static_cast<float*>(c->buf[c->cur ^ 1]), c->g, P, r, u, v,
+        1.0 / u0, cl->wb, cl->w, scale);
     if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
     c->cur ^= 1;
     c->steps += 1;

@@ -31,7 +31,7 @@ EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_st
             "lbm_batch_step", "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_autotune",
             "lbm_closure_create", "lbm_closure_destroy", "lbm_closure_set_weights", "lbm_closure_get_weights",
             "lbm_closure_forward", "lbm_closure_train_step", "lbm_closure_gradients", "lbm_closure_features",
-            "lbm_closure_coarsen", "lbm_step_closure"]
+            "lbm_closure_coarsen", "lbm_step_closure", "lbm_closure_apply"]
 
 
 class lbm_params(ctypes.Structure):
@@ -297,6 +297,7 @@ def _closure_sigs(lib):
         "lbm_closure_coarsen": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, vp, vp, vp,
                                                vp, vp]),
         "lbm_step_closure": (ctypes.c_int, [vp, vp, dp, ctypes.c_int]),
+        "lbm_closure_apply": (ctypes.c_int, [vp, vp, dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -373,3 +374,7 @@ def lbm_closure_coarsen(rho, ux, uy, nx, ny, factor, u0, rho_c, ux_c, uy_c, y, s
 
 def lbm_step_closure(ctx, cl, u0, n=1):
     return _check(_cl().lbm_step_closure(ctx, cl, float(u0), int(n)), ctx, "lbm_step_closure")
+
+
+def lbm_closure_apply(ctx, y, u0):
+    return _check(_cl().lbm_closure_apply(ctx, _dptr(y), float(u0)), ctx, "lbm_closure_apply")

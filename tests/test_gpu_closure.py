@@ -160,3 +160,40 @@ def test_trained_closure_beats_plain_rr_on_the_coarse_grid():
     plain = np.mean([r["spectrum_err"] for r in res["plain"]])
     closure = np.mean([r["spectrum_err"] for r in res["closure"]])
     assert closure < plain
+
+
+@pytest.mark.parametrize("bc_x", ["periodic", "zero_gradient"])
+def test_fused_closure_step_equals_the_composed_stages(bc_x):
+    """lbm_step_closure (moments, then features + network + collision fused per 32 x 4 tile) against
+    lbm_moments + lbm_closure_features + lbm_closure_forward + lbm_closure_apply, bit for bit, on a grid
+    that is ragged in both directions, over three steps with a network whose corrections are not small."""
+    torch, m = torch_mod(), lib()
+    nx, ny, u0 = 80, 50, 0.05
+    fl = wl.random_fields(nx, ny, seed=21, u_scale=0.04)
+    bc = m.PERIODIC if bc_x == "periodic" else m.ZERO_GRADIENT
+    ps = m.make_params("D2Q9", nx, ny, tau=0.6, collision="rr", hermite_order=2, storage="f32", bc_x=bc)
+    c1, c2 = m.lbm_create(ps), m.lbm_create(ps)
+    cl = m.lbm_closure_create()
+    try:
+        m.lbm_closure_set_weights(cl, wl.closure_initial_weights(13, out_scale=1.0))
+        for c in (c1, c2):
+            m.lbm_init(c, fl.rho, fl.ux, fl.uy)
+        n = nx * ny
+        r, u, v = (torch.zeros((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3))
+        x = torch.zeros((n, mlp.NI), dtype=torch.bfloat16, device="cuda")
+        y = torch.zeros((n, mlp.NO), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            m.lbm_step_closure(c1, cl, u0, 1)
+            m.lbm_moments(c2, r, u, v)
+            m.lbm_closure_features(r, u, v, nx, ny, u0, x, None)
+            m.lbm_closure_forward(cl, x, n, y, None)
+            assert float(y[:, :3].abs().max()) > 1e-2  # the correction is active
+            m.lbm_closure_apply(c2, y, u0)
+        f1, f2 = np.empty((9, ny, nx)), np.empty((9, ny, nx))
+        m.lbm_get_populations(c1, f1)
+        m.lbm_get_populations(c2, f2)
+        assert np.array_equal(f1, f2)
+    finally:
+        m.lbm_closure_destroy(cl)
+        m.lbm_destroy(c1)
+        m.lbm_destroy(c2)
