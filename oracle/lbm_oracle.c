@@ -313,7 +313,17 @@ static int resolve_orders(const orc_params *p, const orc_lattice *L, int *neq, i
   if (*nreg < 2 || *nreg > L->nmax) return -1;
   if (p->thermal && p->lattice != ORC_D2V37) return -1;
   if (!(p->tau > 0.5)) return -1;
+  if (p->tau3 < 0.0 || p->tau4 < 0.0 || (p->tau3 > 0.0 && !(p->tau3 > 0.5)) || (p->tau4 > 0.0 && !(p->tau4 > 0.5)))
+    return -1;
+  if (p->collision == ORC_BGK && (p->tau3 > 0.0 || p->tau4 > 0.0)) return -1;
   return 0;
+}
+
+/* Relaxation time of the order-n coefficients of f^(1) (n >= 2). */
+static double tau_of_order(const orc_params *p, int n) {
+  if (n == 3 && p->tau3 > 0.0) return p->tau3;
+  if (n == 4 && p->tau4 > 0.0) return p->tau4;
+  return p->tau;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -323,7 +333,8 @@ static int resolve_orders(const orc_params *p, const orc_lattice *L, int *neq, i
 /*  RR  (Sec. II.E):  a1^(2) projected; isothermal a1^(n>=3) by Eq.          */
 /*      (MalaspinasRecursiveRelation); thermal a1^(3) by App. C steps 1-4,   */
 /*      a1^(n>=4) by Eq. (RecursiveRelation_ThermalCase).                    */
-/*  PR/RR rebuild (Eq. RegularizedCollision): f* = f^(0) + (1-1/tau) f^(1).  */
+/*  PR/RR rebuild (Eq. GenRegCollision with one relaxation time per order,   */
+/*      Sec. II.B): f* = f^(0) + sum_n (1 - 1/tau_n) f^(1,n), tau_2 = tau.   */
 /* ------------------------------------------------------------------------ */
 int orc_collide(const orc_params *p, const double *f_in, double *f_out) {
   orc_lattice L;
@@ -377,9 +388,13 @@ int orc_collide(const orc_params *p, const double *f_in, double *f_out) {
     return -1;
   }
 
-  double fneq[ORC_MAXQ];
-  orc_expand(&L, 2, nreg, a1, fneq);
-  for (int i = 0; i < L.V; i++) f_out[i] = feq[i] + (1.0 - 1.0 / p->tau) * fneq[i];
+  for (int i = 0; i < L.V; i++) f_out[i] = feq[i];
+  for (int n = 2; n <= nreg; n++) {
+    double fn[ORC_MAXQ];
+    orc_expand(&L, n, n, a1, fn);
+    const double om1 = 1.0 - 1.0 / tau_of_order(p, n);
+    for (int i = 0; i < L.V; i++) f_out[i] += om1 * fn[i];
+  }
   return 0;
 }
 

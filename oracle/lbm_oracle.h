@@ -57,8 +57,10 @@ typedef struct {
   int collision;      /* ORC_BGK / ORC_PR / ORC_RR */
   int thermal;        /* 1: theta from the energy moment (D2V37 only); 0: theta = 1 */
   int nx, ny;
-  double tau;         /* relaxation time tau-bar of the discrete scheme (Sec. III.A) */
+  double tau;         /* relaxation time tau-bar of the discrete scheme (Sec. III.A); that of order 2 */
   int bc_x, bc_y;     /* ORC_PERIODIC / ORC_ZERO_GRADIENT */
+  double tau3, tau4;  /* relaxation times of the order-3 and order-4 coefficients of f^(1) (Eq.
+                         GenRegCollision with one time per order, Sec. II.B); 0 = tau.  PR/RR only */
 } orc_params;
 
 /* Lattice of Tab. I (0 on success, -1 for an unknown id). */

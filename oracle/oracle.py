@@ -49,7 +49,8 @@ class OrcLattice(ctypes.Structure):
 class OrcParams(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("hermite_order", ctypes.c_int), ("reg_order", ctypes.c_int),
                 ("collision", ctypes.c_int), ("thermal", ctypes.c_int), ("nx", ctypes.c_int),
-                ("ny", ctypes.c_int), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int)]
+                ("ny", ctypes.c_int), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("tau3", ctypes.c_double), ("tau4", ctypes.c_double)]
 
 
 _lib = None
@@ -120,9 +121,12 @@ def a1_third_thermal(ux, uy, a1_2, a1_3_proj) -> np.ndarray:
 
 
 def params(lattice_, nx, ny, tau, collision="rr", hermite_order=2, reg_order=0, thermal=False,
-           bc_x=PERIODIC, bc_y=PERIODIC) -> OrcParams:
+           bc_x=PERIODIC, bc_y=PERIODIC, tau3=0.0, tau4=0.0) -> OrcParams:
+    """tau is the order-2 (viscous) relaxation time; tau3 / tau4 those of the order-3 / order-4
+    coefficients of f^(1) (0 = tau)."""
     return OrcParams(LATTICE_NAMES.get(lattice_, lattice_), hermite_order, reg_order,
-                     COLLISION_NAMES.get(collision, collision), int(thermal), nx, ny, float(tau), bc_x, bc_y)
+                     COLLISION_NAMES.get(collision, collision), int(thermal), nx, ny, float(tau), bc_x, bc_y,
+                     float(tau3), float(tau4))
 
 
 def expand(lat, nmin, nmax, coef) -> np.ndarray:
