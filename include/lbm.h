@@ -81,6 +81,10 @@ typedef struct {
   double rho0;       /* shifted storage reference density; 0 = 1 */
   double store_scale;/* shifted storage scale s, a power of two; 0 = 1 */
   void *stream;      /* cudaStream_t all work of the context is issued on; NULL = legacy default stream */
+  double tau3, tau4; /* relaxation times tau-bar of the order-3 and order-4 coefficients of f^(1) (Eq.
+                        GenRegCollision with one time per order, Sec. II.B: tau3 sets the heat
+                        conductivity, Pr = (tau - 1/2) / (tau3 - 1/2)); 0 = tau.  Each > 1/2 when set;
+                        PR and RR only (LBM_EINVAL with BGK) */
 } lbm_params;
 
 /* Lattice description in the library's velocity order (Tab. I).  Any output

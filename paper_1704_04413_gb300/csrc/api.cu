@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <initializer_list>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -56,15 +57,22 @@ int lattice_nmax(int lat) { return lat == LBM_D2V17 ? 3 : 4; }
 
 }  // namespace
 
-cudaError_t lbm_ctx_launch_step(lbm_ctx* c, const void* fin, void* fout) {
+CollParamsD lbm_ctx_coll_params(const lbm_ctx* c) {
   CollParamsD pd;
   pd.omega = 1.0 / c->tau;
   pd.om1 = 1.0 - 1.0 / c->tau;
+  pd.om1_3 = 1.0 - 1.0 / c->tau3;
+  pd.om1_4 = 1.0 - 1.0 / c->tau4;
   pd.neq = c->neq;
   pd.nreg = c->nreg;
   pd.rho0 = c->rho0;
   pd.s = c->s;
   pd.inv_s = 1.0 / c->s;
+  return pd;
+}
+
+cudaError_t lbm_ctx_launch_step(lbm_ctx* c, const void* fin, void* fout) {
+  const CollParamsD pd = lbm_ctx_coll_params(c);
   const int coll = c->p.collision;
   switch (c->p.lattice) {
     case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
@@ -160,6 +168,10 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     tau = p->nu / cs2 + 0.5;  // nu = cs^2 (tau - 1/2), Sec. II.B / III.A
   }
   if (!(tau > 0.5) || !std::isfinite(tau)) return LBM_EINVAL;
+  // one relaxation time per order of f^(1) (Eq. GenRegCollision): unset = tau, PR / RR only
+  for (double tn : {p->tau3, p->tau4})
+    if (tn != 0 && (!(tn > 0.5) || !std::isfinite(tn))) return LBM_EINVAL;
+  if (p->collision == LBM_BGK && (p->tau3 != 0 || p->tau4 != 0)) return LBM_EINVAL;
   const double rho0 = p->rho0 == 0 ? 1.0 : p->rho0;
   const double s = p->store_scale == 0 ? 1.0 : p->store_scale;
   if (!(rho0 > 0) || !std::isfinite(rho0) || !is_pow2(s)) return LBM_EINVAL;
@@ -176,6 +188,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
   c->nreg = p->reg_order == 0 ? nmax : p->reg_order;
   c->cs2 = cs2;
   c->tau = tau;
+  c->tau3 = p->tau3 != 0 ? p->tau3 : tau;
+  c->tau4 = p->tau4 != 0 ? p->tau4 : tau;
   c->rho0 = rho0;
   c->s = s;
   c->elem = prec == PREC_F64 ? 8 : prec == PREC_F32 ? 4 : 2;  // the three 16-bit formats

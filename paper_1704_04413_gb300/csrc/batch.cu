@@ -134,15 +134,7 @@ BatchDesc make_desc(const lbm_batch* b, int lattice, int flip) {
     I.fin = c->buf[cur];
     I.fout = c->buf[cur ^ 1];
     I.g = c->g;
-    CollParamsD pd;
-    pd.omega = 1.0 / c->tau;
-    pd.om1 = 1.0 - 1.0 / c->tau;
-    pd.neq = c->neq;
-    pd.nreg = c->nreg;
-    pd.rho0 = c->rho0;
-    pd.s = c->s;
-    pd.inv_s = 1.0 / c->s;
-    I.P = cast_params<F2>(pd);
+    I.P = cast_params<F2>(lbm_ctx_coll_params(c));
     I.ntx = (c->p.nx + 2 * b->threads - 1) / (2 * b->threads);
     I.item0 = item;
     item += (long long)I.ntx * ((c->p.ny + b->rows - 1) / b->rows);

@@ -764,15 +764,7 @@ static bool closure_ctx_ok(const lbm_ctx* c) {
 }
 
 static lbm::CollParams<float> closure_coll_params(const lbm_ctx* c) {
-  lbm::CollParamsD pd;
-  pd.omega = 1.0 / c->tau;
-  pd.om1 = 1.0 - 1.0 / c->tau;
-  pd.neq = c->neq;
-  pd.nreg = c->nreg;
-  pd.rho0 = c->rho0;
-  pd.s = c->s;
-  pd.inv_s = 1.0 / c->s;
-  return lbm::cast_params<float>(pd);
+  return lbm::cast_params<float>(lbm_ctx_coll_params(c));
 }
 
 int lbm_closure_apply(lbm_ctx* c, const float* y, double u0) {

@@ -36,7 +36,9 @@ struct Scalar<F2> {
 template <class Real>
 struct CollParams {
   Real omega;  // 1 / tau
-  Real om1;    // 1 - 1 / tau
+  Real om1;    // 1 - 1 / tau (order 2 of f^(1); BGK)
+  Real om1_3;  // 1 - 1 / tau_3, 1 - 1 / tau_4: one relaxation time per order (Eq. GenRegCollision)
+  Real om1_4;
   int neq;     // highest order of f^(0)
   int nreg;    // highest order of f^(1)
   Real rho0;   // shift of low-precision storage
@@ -219,7 +221,8 @@ __host__ __device__ constexpr double kappa(int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
-// One collision.  q holds the pulled populations in storage representation
+// One collision.  PR/RR rebuild with one relaxation time per order of f^(1) (Eq. GenRegCollision with
+// tau_{n,alpha} -> tau_n): f* = f^(0) + sum_n (1 - 1/tau_n) f^(1,n).  q holds the pulled populations in storage representation
 // (converted to Real) and receives the post-collision ones.
 // ---------------------------------------------------------------------------
 // With CLOSURE, da[0..2] is added to the projected a1^(2) (xx, xy, yy) before the recursion (the
@@ -377,7 +380,7 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
         if constexpr (COLL == COLL_BGK) {
           v *= P.omega;
         } else if constexpr (n >= 2) {
-          if (n <= P.nreg) v += P.om1 * B[a][b];
+          if (n <= P.nreg) v += (n == 2 ? P.om1 : (n == 3 ? P.om1_3 : P.om1_4)) * B[a][b];
         }
         if constexpr (SHIFTED) v *= P.s;
         C[a][b] = v * Real(sc);

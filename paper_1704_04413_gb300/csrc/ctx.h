@@ -13,6 +13,7 @@ struct lbm_ctx {
   int prec = 0;   // PREC_*
   int neq = 0, nreg = 0;
   double cs2 = 0, tau = 0, rho0 = 1, s = 1;
+  double tau3 = 0, tau4 = 0;  // relaxation times of orders 3 and 4 of f^(1) (= tau unless set)
   size_t elem = 0;  // bytes per stored value
   lbm::StepGeom g{};
   void* buf[2] = {nullptr, nullptr};
@@ -28,6 +29,9 @@ struct lbm_ctx {
   int device = 0;
   char err[256] = {0};
 };
+
+// Collision parameters of a context: relaxation factors, orders, storage shift and scale (api.cu).
+lbm::CollParamsD lbm_ctx_coll_params(const lbm_ctx* c);
 
 // Launch one time step of a context from `fin` to `fout` (api.cu).
 cudaError_t lbm_ctx_launch_step(lbm_ctx* c, const void* fin, void* fout);

@@ -27,7 +27,8 @@ struct StepGeom {
 };
 
 struct CollParamsD {
-  double omega, om1;
+  double omega, om1;  // 1 / tau, 1 - 1 / tau (order 2 of f^(1); BGK)
+  double om1_3, om1_4;  // 1 - 1 / tau_n of the order-3 and order-4 coefficients of f^(1)
   int neq, nreg;
   double rho0, s, inv_s;
 };
@@ -38,6 +39,8 @@ __host__ __device__ inline CollParams<Real> cast_params(const CollParamsD& d) {
   CollParams<Real> p;
   p.omega = Real((Sc)d.omega);
   p.om1 = Real((Sc)d.om1);
+  p.om1_3 = Real((Sc)d.om1_3);
+  p.om1_4 = Real((Sc)d.om1_4);
   p.neq = d.neq;
   p.nreg = d.nreg;
   p.rho0 = Real((Sc)d.rho0);

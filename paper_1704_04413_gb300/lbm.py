@@ -39,7 +39,8 @@ class lbm_params(ctypes.Structure):
                 ("collision", ctypes.c_int), ("thermal", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nu", ctypes.c_double), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
                 ("storage", ctypes.c_int), ("compute", ctypes.c_int), ("rho0", ctypes.c_double),
-                ("store_scale", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("store_scale", ctypes.c_double), ("stream", ctypes.c_void_p), ("tau3", ctypes.c_double),
+                ("tau4", ctypes.c_double)]
 
 
 class LbmError(RuntimeError):
@@ -139,12 +140,12 @@ def lbm_lattice_info(lattice):
 
 def make_params(lattice="D2Q9", nx=64, ny=64, tau=0.0, nu=0.0, collision="rr", hermite_order=2, reg_order=0,
                 thermal=False, bc_x=PERIODIC, bc_y=PERIODIC, storage="f32", rho0=0.0, store_scale=0.0,
-                stream=None) -> lbm_params:
+                stream=None, tau3=0.0, tau4=0.0) -> lbm_params:
     st = STORAGES.get(storage, storage)
     compute = F64 if st == F64 else F32
     return lbm_params(LATTICES.get(lattice, lattice), hermite_order, reg_order,
                       COLLISIONS.get(collision, collision), int(thermal), nx, ny, float(nu), float(tau), bc_x, bc_y,
-                      st, compute, float(rho0), float(store_scale), stream)
+                      st, compute, float(rho0), float(store_scale), stream, float(tau3), float(tau4))
 
 
 def lbm_create(params: lbm_params):

@@ -64,6 +64,9 @@ def test_invalid_parameters_are_rejected_on_host(lbm):
         dict(lattice="D2Q9", nx=0),
         dict(lattice="D2Q9", store_scale=3.0, storage="f16"),
         dict(lattice="D2Q9", bc_x=7),
+        dict(lattice="D2Q9", tau3=0.5),                    # per-order time must exceed 1/2
+        dict(lattice="D2Q9", tau4=-1.0),
+        dict(lattice="D2Q9", collision="bgk", tau3=0.9),   # one time per order needs PR or RR
     ]
     for kw in bad:
         kw.setdefault("tau", 0.8)

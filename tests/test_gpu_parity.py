@@ -56,6 +56,25 @@ def test_one_step_matches_oracle(name, coll, neq, nreg, thermal, storage):
     assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
 
 
+PER_ORDER = [m for m in MODES if m[1] != "bgk" and (m[3] == 0 or m[3] >= 3)]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("name,coll,neq,nreg,thermal", PER_ORDER)
+def test_one_step_with_per_order_times_matches_oracle(name, coll, neq, nreg, thermal, storage):
+    """Eq. GenRegCollision with one relaxation time per order of f^(1): tau_2 = 0.62, tau_3 = 0.55,
+    tau_4 = 1.3 (order 4 only where the lattice keeps it)."""
+    nx, ny, tau, tau3, tau4 = 300, 5, 0.62, 0.55, 1.3
+    f = oracle_state(name, nx, ny, 17, thermal)
+    op = orc.params(name, nx, ny, tau, coll, neq, nreg, thermal=thermal, tau3=tau3, tau4=tau4)
+    ref = orc.step(op, f)
+    with Ctx(name, nx, ny, tau, coll, neq, nreg, storage, thermal, tau3=tau3, tau4=tau4) as c:
+        c.set_oracle_f(f)
+        c.step(1)
+        got = c.get_oracle_f()
+    assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
+
+
 @pytest.mark.parametrize("bcx,bcy", [(1, 0), (0, 1), (1, 1)])
 @pytest.mark.parametrize("name,thermal", [("D2Q9", False), ("D2V17", False), ("D2V37", True)])
 def test_zero_gradient_boundaries_match_oracle(name, thermal, bcx, bcy):

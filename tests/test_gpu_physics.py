@@ -11,7 +11,7 @@ from oracle import oracle as orc
 from oracle import riemann
 from paper_1704_04413_gb300 import workloads as wl
 
-from gpu_util import Ctx, rel_l2
+from gpu_util import Ctx, lib, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -58,3 +58,34 @@ def test_shear_wave_decay_on_gpu(name, neq):
         ux = c.moments()[1]
     A = 2.0 / ny * np.sum(ux[:, 0] * np.sin(k * np.arange(ny)))
     assert abs(A / (amp * np.exp(-nu * k * k * T)) - 1.0) < 0.01
+
+
+@pytest.mark.parametrize("coll", ["pr", "rr"])
+def test_prandtl_number_from_the_order3_time(coll):
+    """Thermal D2V37, FP32: an isobaric temperature wave decays at alpha k^2 with alpha = cs^2 (tau_3 - 1/2)
+    while tau_2 = 0.8 fixes the viscosity (Pr = (tau_2 - 1/2) / (tau_3 - 1/2) = 3 and 0.6 here)."""
+    m = lib()
+    V, cx, cy, w, cs2 = m.lbm_lattice_info("D2V37")
+    nx, ny = 64, 2
+    k = 2 * np.pi / nx
+    x = np.arange(nx) + 0.5
+    th = np.tile(1 + 0.01 * np.sin(k * x), (ny, 1))
+    zero = np.zeros_like(th)
+    for tau3 in (0.6, 1.0):
+        ctx = m.lbm_create(m.make_params("D2V37", nx, ny, tau=0.8, collision=coll, hermite_order=4, thermal=True,
+                                         storage="f32", tau3=tau3))
+        try:
+            m.lbm_init(ctx, 1.0 / th, zero, zero, th)
+            ts, amps = [], []
+            T = np.empty_like(th)
+            for t in range(0, 601, 20):
+                if t:
+                    m.lbm_step(ctx, 20)
+                m.lbm_moments(ctx, None, None, None, T)
+                ts.append(t)
+                amps.append(2 * np.mean((T - T.mean()) * np.sin(k * x)[None, :]))
+        finally:
+            m.lbm_destroy(ctx)
+        ts, amps = np.array(ts), np.array(amps)
+        rate = -np.polyfit(ts[ts >= 100], np.log(amps[ts >= 100]), 1)[0]
+        assert rate == pytest.approx(cs2 * (tau3 - 0.5) * k * k, rel=0.02)
