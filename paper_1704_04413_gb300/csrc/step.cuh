@@ -186,6 +186,12 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
 #ifndef LBM_STEP2_MINB_LARGE
 #define LBM_STEP2_MINB_LARGE 2
 #endif
+#ifndef LBM_STEP_PAIRS_LARGE_16
+#define LBM_STEP_PAIRS_LARGE_16 1
+#endif
+#ifndef LBM_STEP_PAIRS_LARGE_16_MIN
+#define LBM_STEP_PAIRS_LARGE_16_MIN (1LL << 21)
+#endif
 
 template <class S>
 __device__ __forceinline__ F2 ld_pair(const char* p);
@@ -384,7 +390,20 @@ inline cudaError_t launch_step_t(const void* fin, void* fout, const StepGeom& g,
 template <class L, int COLL, bool THERMAL>
 inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const StepGeom& g,
                                     const CollParamsD& pd, cudaStream_t st) {
-  // two cells per thread pay off while the pair's registers stay low (D2Q9, D2V17); D2V37 keeps one
+  // Two cells per thread pay off while the pair's registers stay low (D2Q9, D2V17).  D2V37 keeps one
+  // cell per thread in FP32 and FP64 (HBM-bound: its 20 resident warps per SM keep more bytes in flight
+  // than the pair kernel's 16), but with 16-bit storage, which is issue-bound, the packed FP32x2
+  // arithmetic wins from LBM_STEP_PAIRS_LARGE_16_MIN cells up (measured on GB300 at 4096^2: BF16 27.4
+  // -> 36.6 GLUPS, FP16 27.4 -> 31.7, fixed point 26.1 -> 30.7); below that the grid is a few waves and
+  // the scalar kernel's shorter blocks are as fast or faster.
+  if constexpr (!THERMAL && LBM_STEP_PAIRS_LARGE_16 && L::Q > 20) {
+    if ((long long)g.nx * g.ny >= LBM_STEP_PAIRS_LARGE_16_MIN) switch (prec) {
+      case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st);
+      case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st);
+      case PREC_I16: return launch_step2_t<L, COLL, short>(fin, fout, g, pd, st);
+      default: break;
+    }
+  }
   if constexpr (!THERMAL && LBM_STEP_PAIRS && L::Q <= 20) {
     switch (prec) {
       case PREC_F64: return launch_step_t<L, COLL, THERMAL, double, double>(fin, fout, g, pd, st);

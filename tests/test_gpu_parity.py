@@ -166,7 +166,7 @@ def test_diagnostics_match_oracle():
     assert np.max(np.abs(d - d_o) / np.abs(d_o)) <= 1e-9
 
 
-@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
 @pytest.mark.parametrize("name,thermal", [("D2Q9", False), ("D2V17", False), ("D2V37", False), ("D2V37", True)])
 def test_shifted_low_precision_storage(name, thermal, storage, tol):
     """Shifted FP16/BF16 storage g = (f/w - rho0) s: one step against the oracle, error relative to
@@ -266,3 +266,28 @@ def test_full_size_sampled_parity_d2v37():
     ref = orc.step_cells(op, f, cells)
     got_s = got.reshape(Lt.V, -1)[:, cells]
     assert pop_rel(got_s, ref.T, Lt.w) <= 1e-6
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
+def test_large_grid_16bit_d2v37_sampled_parity(storage, tol):
+    """2048 x 1024 D2V37 RR shear layer with 16-bit storage: above 2^21 cells the step runs two cells per
+    thread in packed FP32x2 (below it, one); one step checked on 1500 sampled cells (edges included)
+    against the oracle, error relative to the deviation scale the format resolves."""
+    name, nx, ny = "D2V37", 2048, 1024
+    Lt = orc.lattice(name)
+    u0, nu, _ = wl.shear_layer_params(nx, np.sqrt(Lt.cs2), 0.1, 3e4)
+    fl = wl.double_shear_layer(nx, u0, ny=ny)
+    tau = orc.tau_from_nu(Lt.cs2, nu)
+    op = orc.params(name, nx, ny, tau, "rr", 4)
+    f = orc.init(op, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+    rng = np.random.default_rng(1)
+    cells = np.concatenate([rng.integers(0, nx * ny, 1400), np.arange(0, nx, 23), np.arange(0, nx * ny, nx * 97)[:10],
+                            [nx - 1, nx * ny - 1, nx * (ny - 1), 2 * nx - 1, 2 * nx]])
+    with Ctx(name, nx, ny, tau, "rr", 4, 0, storage) as c:
+        c.set_oracle_f(f)
+        c.step(1)
+        got = c.get_oracle_f().reshape(Lt.V, -1)[:, cells]
+    ref = orc.step_cells(op, f, cells).T
+    w = Lt.w[:, None]
+    dev = np.abs(ref / w - 1.0).max()
+    assert np.max(np.abs(got - ref) / w) <= tol * dev
