@@ -240,6 +240,20 @@ void orc_a1_recursive(double cs2, double rho, double ux, double uy, double theta
  *                                - G_a delta_{bg} - G_b delta_{ag} - G_g delta_{ab}
  * (with G = mu cs^2 grad theta) gives one estimate of G_g when solved for it;
  * the D estimates are averaged (Eq. TempGradLBM) and a1^(3) is rebuilt. */
+/* Eq. a1Rec (App. C step 4): a1^(3)_abg = u_a a1_bg + u_b a1_ag + u_g a1_ab - (delta_bg G_a + delta_ag G_b +
+ * delta_ab G_g), with G_g = mu cs^2 d_g theta. */
+static void a1_third_from_gradients(double ux, double uy, const double *a1_2, const double *G, double *a1_3) {
+  double u[2] = {ux, uy};
+  for (int t = 0; t < 8; t++) {
+    int a = t & 1, b = (t >> 1) & 1, g = (t >> 2) & 1;
+    double v = u[a] * a1_2[pair_tuple(b, g)] + u[b] * a1_2[pair_tuple(a, g)] + u[g] * a1_2[pair_tuple(a, b)];
+    if (b == g) v -= G[a];
+    if (a == g) v -= G[b];
+    if (a == b) v -= G[g];
+    a1_3[t] = v;
+  }
+}
+
 void orc_a1_third_thermal(double ux, double uy, const double *a1_2, const double *a1_3_proj, double *a1_3) {
   const int D = 2;
   double u[2] = {ux, uy};
@@ -254,14 +268,7 @@ void orc_a1_third_thermal(double ux, double uy, const double *a1_2, const double
     }
     G[g] = acc / D;
   }
-  for (int t = 0; t < 8; t++) {
-    int a = t & 1, b = (t >> 1) & 1, g = (t >> 2) & 1;
-    double v = u[a] * a1_2[pair_tuple(b, g)] + u[b] * a1_2[pair_tuple(a, g)] + u[g] * a1_2[pair_tuple(a, b)];
-    if (b == g) v -= G[a];
-    if (a == g) v -= G[b];
-    if (a == b) v -= G[g];
-    a1_3[t] = v;
-  }
+  a1_third_from_gradients(ux, uy, a1_2, G, a1_3);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -316,6 +323,7 @@ static int resolve_orders(const orc_params *p, const orc_lattice *L, int *neq, i
   if (p->tau3 < 0.0 || p->tau4 < 0.0 || (p->tau3 > 0.0 && !(p->tau3 > 0.5)) || (p->tau4 > 0.0 && !(p->tau4 > 0.5)))
     return -1;
   if (p->collision == ORC_BGK && (p->tau3 > 0.0 || p->tau4 > 0.0)) return -1;
+  if (p->a1_source != 0 && (p->a1_source != 1 || p->collision != ORC_RR)) return -1;
   return 0;
 }
 
@@ -336,7 +344,20 @@ static double tau_of_order(const orc_params *p, int n) {
 /*  PR/RR rebuild (Eq. GenRegCollision with one relaxation time per order,   */
 /*      Sec. II.B): f* = f^(0) + sum_n (1 - 1/tau_n) f^(1,n), tau_2 = tau.   */
 /* ------------------------------------------------------------------------ */
+static int collide_cell(const orc_params *p, const double *f_in, const double *grad, double *f_out);
+
 int orc_collide(const orc_params *p, const double *f_in, double *f_out) {
+  if (p->a1_source != 0) return -1;
+  return collide_cell(p, f_in, NULL, f_out);
+}
+
+int orc_collide_fd(const orc_params *p, const double *f_in, const double *grad, double *f_out) {
+  if (p->a1_source != 1 || !grad) return -1;
+  return collide_cell(p, f_in, grad, f_out);
+}
+
+/* grad == NULL: a1 by projection; else a1^(2) (and the thermal temperature gradients) from grad. */
+static int collide_cell(const orc_params *p, const double *f_in, const double *grad, double *f_out) {
   orc_lattice L;
   if (orc_lattice_get(p->lattice, &L)) return -1;
   int neq, nreg;
@@ -369,6 +390,21 @@ int orc_collide(const orc_params *p, const double *f_in, double *f_out) {
   memset(a1, 0, sizeof(a1));
   if (p->collision == ORC_PR) {
     memcpy(a1, a1p, sizeof(a1));
+  } else if (p->collision == ORC_RR && grad) {
+    /* Chapman-Enskog forms of Sec. II.E (App. A) from the finite-difference gradients */
+    const double th = p->thermal ? theta : 1.0;
+    const double pre = -p->tau * rho * L.cs2 * th;
+    const double div = p->thermal ? grad[0] + grad[3] : 0.0; /* (2/D) div u, D = 2 */
+    TEN(a1, 2, pair_tuple(0, 0)) = pre * (2.0 * grad[0] - div);
+    TEN(a1, 2, pair_tuple(1, 1)) = pre * (2.0 * grad[3] - div);
+    TEN(a1, 2, pair_tuple(0, 1)) = pre * (grad[1] + grad[2]);
+    TEN(a1, 2, pair_tuple(1, 0)) = pre * (grad[1] + grad[2]);
+    if (p->thermal && nreg >= 3) {
+      const double mu_cs2 = tau_of_order(p, 3) * rho * L.cs2 * theta * L.cs2;
+      const double G[2] = {mu_cs2 * grad[4], mu_cs2 * grad[5]};
+      a1_third_from_gradients(ux, uy, &TEN(a1, 2, 0), G, &TEN(a1, 3, 0));
+    }
+    orc_a1_recursive(L.cs2, rho, ux, uy, theta, p->thermal, nreg, a0, a1);
   } else if (p->collision == ORC_RR) {
     for (int t = 0; t < 4; t++) TEN(a1, 2, t) = TEN(a1p, 2, t);
     if (p->thermal) {
@@ -424,22 +460,61 @@ static void gather_cell(const orc_params *p, const orc_lattice *L, const double 
   }
 }
 
+/* Moments rho, ux, uy, theta of every cell after streaming (the fields the collision sees), m[4][ny][nx]. */
+static void stream_moments(const orc_params *p, const orc_lattice *L, const double *f_in, double *m) {
+  long long plane = (long long)p->nx * p->ny;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < p->ny; y++) {
+    double fc[ORC_MAXQ];
+    for (int x = 0; x < p->nx; x++) {
+      long long c = (long long)y * p->nx + x;
+      gather_cell(p, L, f_in, x, y, fc);
+      orc_cell_moments(L, p->thermal, fc, &m[c], &m[plane + c], &m[2 * plane + c], &m[3 * plane + c]);
+    }
+  }
+}
+
+/* Second-order central differences of ux, uy, theta at (x, y); neighbours follow the streaming rule (periodic
+ * wrap, or the clamped edge cell on a zero-gradient axis, which makes the edge difference one-sided). */
+static void central_gradients(const orc_params *p, const double *m, int x, int y, double *grad) {
+  long long plane = (long long)p->nx * p->ny;
+  int xp = src_index(x, -1, p->nx, p->bc_x), xm = src_index(x, 1, p->nx, p->bc_x);
+  int yp = src_index(y, -1, p->ny, p->bc_y), ym = src_index(y, 1, p->ny, p->bc_y);
+  const double *ux = m + plane, *uy = m + 2 * plane, *th = m + 3 * plane;
+  long long ex = (long long)y * p->nx + xp, wx = (long long)y * p->nx + xm;
+  long long ny_ = (long long)yp * p->nx + x, sy = (long long)ym * p->nx + x;
+  grad[0] = 0.5 * (ux[ex] - ux[wx]);
+  grad[1] = 0.5 * (ux[ny_] - ux[sy]);
+  grad[2] = 0.5 * (uy[ex] - uy[wx]);
+  grad[3] = 0.5 * (uy[ny_] - uy[sy]);
+  grad[4] = 0.5 * (th[ex] - th[wx]);
+  grad[5] = 0.5 * (th[ny_] - th[sy]);
+}
+
 int orc_step(const orc_params *p, const double *f_in, double *f_out) {
   orc_lattice L;
   if (orc_lattice_get(p->lattice, &L)) return -1;
   int neq, nreg;
   if (resolve_orders(p, &L, &neq, &nreg)) return -1;
   long long plane = (long long)p->nx * p->ny;
+  double *m = NULL;
+  if (p->a1_source == 1) {
+    m = (double *)malloc(sizeof(double) * 4 * (size_t)plane);
+    if (!m) return -1;
+    stream_moments(p, &L, f_in, m);
+  }
   int err = 0;
 #pragma omp parallel for schedule(static) reduction(| : err)
   for (int y = 0; y < p->ny; y++) {
-    double fc[ORC_MAXQ], fo[ORC_MAXQ];
+    double fc[ORC_MAXQ], fo[ORC_MAXQ], grad[ORC_NGRAD];
     for (int x = 0; x < p->nx; x++) {
       gather_cell(p, &L, f_in, x, y, fc);
-      err |= orc_collide(p, fc, fo) != 0;
+      if (m) central_gradients(p, m, x, y, grad);
+      err |= collide_cell(p, fc, m ? grad : NULL, fo) != 0;
       for (int i = 0; i < L.V; i++) f_out[i * plane + (long long)y * p->nx + x] = fo[i];
     }
   }
+  free(m);
   return err ? -1 : 0;
 }
 
@@ -448,26 +523,25 @@ int orc_step_cells(const orc_params *p, const double *f_in, int ncell, const lon
   if (orc_lattice_get(p->lattice, &L)) return -1;
   int neq, nreg;
   if (resolve_orders(p, &L, &neq, &nreg)) return -1;
+  double *m = NULL;
+  if (p->a1_source == 1) {
+    m = (double *)malloc(sizeof(double) * 4 * (size_t)p->nx * (size_t)p->ny);
+    if (!m) return -1;
+    stream_moments(p, &L, f_in, m);
+  }
   int err = 0;
 #pragma omp parallel for schedule(static) reduction(| : err)
   for (int k = 0; k < ncell; k++) {
-    double fc[ORC_MAXQ];
+    double fc[ORC_MAXQ], grad[ORC_NGRAD];
     int x = (int)(cells[k] % p->nx), y = (int)(cells[k] / p->nx);
     gather_cell(p, &L, f_in, x, y, fc);
-    err |= orc_collide(p, fc, f_out + (long long)k * L.V) != 0;
+    if (m) central_gradients(p, m, x, y, grad);
+    err |= collide_cell(p, fc, m ? grad : NULL, f_out + (long long)k * L.V) != 0;
   }
+  free(m);
   return err ? -1 : 0;
 }
 
-/* ------------------------------------------------------------------------ */
-/* Initial state (Sec. III.B): f = f^(0) + f^(1), f^(1) from analytic        */
-/* velocity gradients through the Chapman-Enskog a1^(2) (App. A):            */
-/*   thermal:    a1_ab = -tau rho cs^2 theta (d_a u_b + d_b u_a - (2/D) delta_ab div u)  */
-/*   isothermal: a1_ab = -tau rho cs^2 (d_a u_b + d_b u_a)                    */
-/* and a1^(n>=3) by the same recursions as the RR step (no temperature       */
-/* gradient is supplied, so the thermal a1^(3) is the symmetric u a1^(2)     */
-/* sum).  The expansion covers every kept order 2..nmax of the lattice.      */
-/* ------------------------------------------------------------------------ */
 int orc_init(const orc_params *p, const double *rho, const double *ux, const double *uy, const double *T,
              const double *grad_u, double *f) {
   orc_lattice L;

@@ -61,7 +61,14 @@ typedef struct {
   int bc_x, bc_y;     /* ORC_PERIODIC / ORC_ZERO_GRADIENT */
   double tau3, tau4;  /* relaxation times of the order-3 and order-4 coefficients of f^(1) (Eq.
                          GenRegCollision with one time per order, Sec. II.B); 0 = tau.  PR/RR only */
+  int a1_source;      /* RR only: 0 = a1^(2) (and the thermal a1^(3)) by projection of f - f^(0) (Eq. a12Proj,
+                         Eq. TempGradLBM); 1 = by finite differences of the velocity (and temperature)
+                         field (Sec. II.E: "or using finite differences") */
 } orc_params;
+
+/* Gradients handed to the finite-difference collision, per cell:
+ * d ux/dx, d ux/dy, d uy/dx, d uy/dy, d theta/dx, d theta/dy. */
+#define ORC_NGRAD 6
 
 /* Lattice of Tab. I (0 on success, -1 for an unknown id). */
 int orc_lattice_get(int lattice, orc_lattice *out);
@@ -91,8 +98,15 @@ void orc_expand(const orc_lattice *L, int nmin, int nmax, const double *coef, do
 void orc_cell_moments(const orc_lattice *L, int thermal, const double *f, double *rho, double *ux, double *uy,
                       double *theta);
 
-/* Collision of one cell (post-streaming f_in[V] -> post-collision f_out[V]). 0 on success. */
+/* Collision of one cell (post-streaming f_in[V] -> post-collision f_out[V]). 0 on success; -1 when
+ * p->a1_source asks for gradients (use orc_collide_fd). */
 int orc_collide(const orc_params *p, const double *f_in, double *f_out);
+
+/* The same with a1 built from the given gradients grad[ORC_NGRAD] (RR with a1_source = 1):
+ *   a1^(2)_ab = -tau rho cs^2 theta (d_a u_b + d_b u_a - delta_ab div u)   (thermal; D = 2)
+ *   a1^(2)_ab = -tau rho cs^2 (d_a u_b + d_b u_a)                           (isothermal)
+ * and, thermal, mu cs^2 d_g theta = tau_3 rho cs^4 theta d_g theta in place of Eq. TempGradLBM. */
+int orc_collide_fd(const orc_params *p, const double *f_in, const double *grad, double *f_out);
 
 /* One full step (pull streaming + collision) on f_in[V][ny][nx] -> f_out. */
 int orc_step(const orc_params *p, const double *f_in, double *f_out);

@@ -50,7 +50,7 @@ class OrcParams(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("hermite_order", ctypes.c_int), ("reg_order", ctypes.c_int),
                 ("collision", ctypes.c_int), ("thermal", ctypes.c_int), ("nx", ctypes.c_int),
                 ("ny", ctypes.c_int), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
-                ("tau3", ctypes.c_double), ("tau4", ctypes.c_double)]
+                ("tau3", ctypes.c_double), ("tau4", ctypes.c_double), ("a1_source", ctypes.c_int)]
 
 
 _lib = None
@@ -121,12 +121,12 @@ def a1_third_thermal(ux, uy, a1_2, a1_3_proj) -> np.ndarray:
 
 
 def params(lattice_, nx, ny, tau, collision="rr", hermite_order=2, reg_order=0, thermal=False,
-           bc_x=PERIODIC, bc_y=PERIODIC, tau3=0.0, tau4=0.0) -> OrcParams:
+           bc_x=PERIODIC, bc_y=PERIODIC, tau3=0.0, tau4=0.0, a1_source=0) -> OrcParams:
     """tau is the order-2 (viscous) relaxation time; tau3 / tau4 those of the order-3 / order-4
-    coefficients of f^(1) (0 = tau)."""
+    coefficients of f^(1) (0 = tau).  a1_source (RR only): 0 projection, 1 finite differences."""
     return OrcParams(LATTICE_NAMES.get(lattice_, lattice_), hermite_order, reg_order,
                      COLLISION_NAMES.get(collision, collision), int(thermal), nx, ny, float(tau), bc_x, bc_y,
-                     float(tau3), float(tau4))
+                     float(tau3), float(tau4), int(a1_source))
 
 
 def expand(lat, nmin, nmax, coef) -> np.ndarray:
@@ -143,6 +143,17 @@ def collide(p: OrcParams, f: np.ndarray) -> np.ndarray:
     out = np.empty_like(f)
     if lib().orc_collide(ctypes.byref(p), _dp(f), _dp(out)) != 0:
         raise ValueError("orc_collide rejected the parameters")
+    return out
+
+
+def collide_fd(p: OrcParams, f: np.ndarray, grad) -> np.ndarray:
+    """One cell's collision with a1 from the given gradients (d ux/dx, d ux/dy, d uy/dx, d uy/dy, d theta/dx,
+    d theta/dy); p.a1_source must be 1."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    out = np.empty_like(f)
+    if lib().orc_collide_fd(ctypes.byref(p), _dp(f), _dp(g), _dp(out)) != 0:
+        raise ValueError("orc_collide_fd rejected the parameters")
     return out
 
 
