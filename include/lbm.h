@@ -46,7 +46,10 @@ extern "C" {
 
 /* boundary of an axis */
 #define LBM_PERIODIC 0
-#define LBM_ZERO_GRADIENT 1 /* a pulled source outside the domain reads the nearest edge cell */
+#define LBM_ZERO_GRADIENT 1
+
+#define LBM_A1_PROJECTION 0
+#define LBM_A1_FINITE_DIFFERENCE 1 /* a pulled source outside the domain reads the nearest edge cell */
 
 /* population storage / compute precision */
 #define LBM_F64 0
@@ -85,6 +88,12 @@ typedef struct {
                         GenRegCollision with one time per order, Sec. II.B: tau3 sets the heat
                         conductivity, Pr = (tau - 1/2) / (tau3 - 1/2)); 0 = tau.  Each > 1/2 when set;
                         PR and RR only (LBM_EINVAL with BGK) */
+  int a1_source;     /* RR only: LBM_A1_PROJECTION (0, Eq. a12Proj and Eq. TempGradLBM) or
+                        LBM_A1_FINITE_DIFFERENCE (1): a1^(2) = -tau rho cs^2 theta (grad u + grad u^T
+                        [- div u I, thermal]) and the thermal temperature-gradient terms from second-order
+                        central differences of the post-streaming fields (Sec. II.E).  Each step is then a
+                        moments pass plus the step kernel; the context keeps 4 fields of the compute type
+                        per cell for it.  LBM_EINVAL for other values, or with BGK / PR */
 } lbm_params;
 
 /* Lattice description in the library's velocity order (Tab. I).  Any output
@@ -189,7 +198,7 @@ int lbm_conservation_noalloc(int lattice, int storage, const void *f, int nx, in
 typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 
 /* One context per entry of ps[0..n-1] (lattice D2Q9 or D2V17, isothermal,
- * compute LBM_F32 with any non-FP64 storage; one collision model, one storage
+ * compute LBM_F32 with any non-FP64 storage, a1 by projection; one collision model, one storage
  * format and one stream for all).  Errors as lbm_create; LBM_EINVAL for
  * n outside [1, LBM_BATCH_MAX] or mixed collision / storage / stream. */
 int lbm_batch_create(const lbm_params *ps, int n, lbm_batch **out);
@@ -267,7 +276,7 @@ int lbm_closure_coarsen(const double *rho, const double *ux, const double *uy, i
  * step (the FP64 moments, then features + network + collision fused per tile of cells); the result is
  * bitwise that of lbm_moments + lbm_closure_features + lbm_closure_forward + lbm_closure_apply.
  * Allocates a work area of 96 B per cell on first use.  LBM_EINVAL unless the context is D2Q9, RR,
- * isothermal, FP32 storage. */
+ * isothermal, FP32 storage, a1 by projection. */
 int lbm_step_closure(lbm_ctx *c, lbm_closure *cl, double u0, int n);
 /* One RR step of such a context with a caller-supplied correction field y[nx*ny][LBM_CLOSURE_OUT]
  * (device, FP32; components 0..2 = xx, xy, yy of Delta a1 / u0^2 scaled as above), enqueued on the

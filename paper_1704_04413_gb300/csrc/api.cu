@@ -63,6 +63,8 @@ CollParamsD lbm_ctx_coll_params(const lbm_ctx* c) {
   pd.om1 = 1.0 - 1.0 / c->tau;
   pd.om1_3 = 1.0 - 1.0 / c->tau3;
   pd.om1_4 = 1.0 - 1.0 / c->tau4;
+  pd.tau = c->tau;
+  pd.tau3 = c->tau3;
   pd.neq = c->neq;
   pd.nreg = c->nreg;
   pd.rho0 = c->rho0;
@@ -75,11 +77,13 @@ cudaError_t lbm_ctx_launch_step(lbm_ctx* c, const void* fin, void* fout) {
   const CollParamsD pd = lbm_ctx_coll_params(c);
   const int coll = c->p.collision;
   switch (c->p.lattice) {
-    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
-    case LBM_D2V17: return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
+    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st);
+    case LBM_D2V17:
+      return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st);
     case LBM_D2V37:
-      return c->p.thermal ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st)
-                          : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, c->dev_err, c->st);
+      return c->p.thermal
+                 ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st)
+                 : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st);
   }
   return cudaErrorInvalidValue;
 }
@@ -130,6 +134,7 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->out4);
   cudaFree(c->dev_err);
   cudaFree(c->closure_buf);
+  cudaFree(c->fd_mom);
   cudaFreeHost(c->host4);
   delete c;
 }
@@ -172,6 +177,9 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
   for (double tn : {p->tau3, p->tau4})
     if (tn != 0 && (!(tn > 0.5) || !std::isfinite(tn))) return LBM_EINVAL;
   if (p->collision == LBM_BGK && (p->tau3 != 0 || p->tau4 != 0)) return LBM_EINVAL;
+  if (p->a1_source != LBM_A1_PROJECTION &&
+      (p->a1_source != LBM_A1_FINITE_DIFFERENCE || p->collision != LBM_RR))
+    return LBM_EINVAL;
   const double rho0 = p->rho0 == 0 ? 1.0 : p->rho0;
   const double s = p->store_scale == 0 ? 1.0 : p->store_scale;
   if (!(rho0 > 0) || !std::isfinite(rho0) || !is_pow2(s)) return LBM_EINVAL;
@@ -210,7 +218,9 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
       (e = cudaMalloc(&c->partials, sizeof(double) * (size_t)lbm_partials_count(c->g))) != cudaSuccess ||
       (e = cudaMalloc(&c->out4, 5 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->dev_err, sizeof(int))) != cudaSuccess ||
-      (e = cudaMallocHost(&c->host4, 5 * sizeof(double))) != cudaSuccess) {
+      (e = cudaMallocHost(&c->host4, 5 * sizeof(double))) != cudaSuccess ||
+      (p->a1_source == LBM_A1_FINITE_DIFFERENCE &&
+       (e = cudaMalloc(&c->fd_mom, 4 * (size_t)p->nx * (size_t)p->ny * (prec == PREC_F64 ? 8 : 4))) != cudaSuccess)) {
     rc = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
     cudaGetLastError();
     lbm_destroy(c);

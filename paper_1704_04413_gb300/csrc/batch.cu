@@ -193,6 +193,7 @@ int lbm_batch_create(const lbm_params* ps, int n, lbm_batch** out) {
     const lbm_params& p = ps[k];
     if (p.lattice != LBM_D2Q9 && p.lattice != LBM_D2V17) return LBM_EINVAL;
     if (p.thermal || p.compute != LBM_F32 || p.storage == LBM_F64) return LBM_EINVAL;
+    if (p.a1_source != LBM_A1_PROJECTION) return LBM_EINVAL;  // the batched kernel projects a1
     if (p.collision != ps[0].collision || p.storage != ps[0].storage || p.stream != ps[0].stream) return LBM_EINVAL;
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();

@@ -760,7 +760,8 @@ int lbm_closure_train_step(lbm_closure* c, const void* x, const float* y, int n,
 }
 
 static bool closure_ctx_ok(const lbm_ctx* c) {
-  return c->p.lattice == LBM_D2Q9 && c->p.collision == LBM_RR && c->prec == lbm::PREC_F32 && !c->p.thermal;
+  return c->p.lattice == LBM_D2Q9 && c->p.collision == LBM_RR && c->prec == lbm::PREC_F32 && !c->p.thermal &&
+         c->p.a1_source == LBM_A1_PROJECTION;
 }
 
 static lbm::CollParams<float> closure_coll_params(const lbm_ctx* c) {

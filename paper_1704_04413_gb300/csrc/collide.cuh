@@ -39,6 +39,7 @@ struct CollParams {
   Real om1;    // 1 - 1 / tau (order 2 of f^(1); BGK)
   Real om1_3;  // 1 - 1 / tau_3, 1 - 1 / tau_4: one relaxation time per order (Eq. GenRegCollision)
   Real om1_4;
+  Real tau, tau3;  // tau_2 and tau_3 themselves (the finite-difference a1 of FD collisions)
   int neq;     // highest order of f^(0)
   int nreg;    // highest order of f^(1)
   Real rho0;   // shift of low-precision storage
@@ -226,9 +227,14 @@ __host__ __device__ constexpr double kappa(int a, int b) {
 // (converted to Real) and receives the post-collision ones.
 // ---------------------------------------------------------------------------
 // With CLOSURE, da[0..2] is added to the projected a1^(2) (xx, xy, yy) before the recursion (the
-// learned coarse-grid closure; closure.cu).
-template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real, bool CLOSURE = false>
-__device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P, const Real* da = nullptr) {
+// learned coarse-grid closure; closure.cu).  With FD (RR only), a1^(2) and the thermal temperature-gradient
+// terms come from the gradients grad[0..5] = d ux/dx, d ux/dy, d uy/dx, d uy/dy, d theta/dx, d theta/dy
+// (Sec. II.E: "or using finite differences"):
+//   a1^(2)_ab = -tau rho cs^2 theta (d_a u_b + d_b u_a - delta_ab div u) (thermal, D = 2), -tau rho cs^2 S
+//   (isothermal); mu cs^2 d_g theta = tau_3 rho cs^4 theta d_g theta in place of Eq. TempGradLBM.
+template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real, bool CLOSURE = false, bool FD = false>
+__device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P, const Real* da = nullptr,
+                                        const Real* grad = nullptr) {
   using Sc = typename Scalar<Real>::type;
   static_assert(!(THERMAL && !__is_same(Sc, Real)), "the thermal path computes one cell per thread");
   constexpr double c2 = L::CS2;
@@ -335,6 +341,23 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
         }
       });
     });
+  } else if constexpr (COLL == COLL_RR && FD) {
+    const Real th = THERMAL ? Real(1) + e * Real(1.0 / c2) : Real(1);
+    const Real pre = -P.tau * rho * Real(c2) * th;
+    const Real div = THERMAL ? grad[0] + grad[3] : Real(0);
+    B[2][0] = pre * (Real(2) * grad[0] - div);
+    B[1][1] = pre * (grad[1] + grad[2]);
+    B[0][2] = pre * (Real(2) * grad[3] - div);
+    a1_third_from_second<L, THERMAL>(ux, uy, B);
+    if constexpr (THERMAL && L::NMAX >= 3) {
+      const Real mu_cs2 = P.tau3 * rho * Real(c2) * th * Real(c2);
+      const Real gx = mu_cs2 * grad[4], gy = mu_cs2 * grad[5];
+      B[3][0] -= Real(3) * gx;
+      B[2][1] -= gy;
+      B[1][2] -= gx;
+      B[0][3] -= Real(3) * gy;
+    }
+    a1_fourth<L, THERMAL>(ux, uy, e, B);
   } else if constexpr (COLL == COLL_RR) {
     B[2][0] = hmom(IC<2>{}, IC<0>{}) - A[2][0];
     B[1][1] = hmom(IC<1>{}, IC<1>{}) - A[1][1];
@@ -408,6 +431,68 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
       else
         q[i] = Real(ref_weight<L, Sc>(i)) + acc;
     });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Macroscopic fields of one cell's pulled populations (Sec. II.A), as the collision computes them: rho and
+// u from the deviations (FP32 or FP64), theta from the FP64 energy moment on thermal lattices (1 otherwise).
+// Used by the moments pass of the finite-difference variant.
+// ---------------------------------------------------------------------------
+template <class L, bool THERMAL, bool SHIFTED, class Real>
+__device__ __forceinline__ void cell_macro(const Real (&q)[L::Q], const CollParams<Real>& P, Real& rho, Real& ux,
+                                           Real& uy, Real& theta) {
+  using Sc = typename Scalar<Real>::type;
+  if constexpr (THERMAL) {
+    double r = 0.0, jx = 0.0, jy = 0.0, e2 = 0.0;
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      constexpr double wi = L::W[i];
+      double fi;
+      if constexpr (SHIFTED)
+        fi = wi * ((double)P.rho0 + (double)q[i] * (double)P.inv_s);
+      else
+        fi = (double)q[i];
+      constexpr double cx = L::CX[i], cy = L::CY[i];
+      r += fi;
+      if constexpr (cx != 0.0) jx += cx * fi;
+      if constexpr (cy != 0.0) jy += cy * fi;
+      if constexpr (cx * cx + cy * cy != 0.0) e2 += (cx * cx + cy * cy) * fi;
+    });
+    const double uxd = jx / r, uyd = jy / r;
+    rho = (Real)r;
+    ux = (Real)uxd;
+    uy = (Real)uyd;
+    theta = (Real)((e2 / r - uxd * uxd - uyd * uyd) / (2.0 * L::CS2));
+  } else {
+    Real d0 = Real(0), dx = Real(0), dy = Real(0);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      constexpr double wf = SHIFTED ? L::W[i] : 1.0;
+      constexpr double cxw = L::CX[i] * wf, cyw = L::CY[i] * wf;
+      Real di;
+      if constexpr (SHIFTED)
+        di = q[i];
+      else
+        di = q[i] - Real(ref_weight<L, Sc>(i));
+      d0 = madd(Real(wf), di, d0);
+      if constexpr (cxw != 0.0) dx = madd(Real(cxw), di, dx);
+      if constexpr (cyw != 0.0) dy = madd(Real(cyw), di, dy);
+    });
+    if constexpr (SHIFTED) {
+      d0 = d0 * P.inv_s;
+      dx = dx * P.inv_s;
+      dy = dy * P.inv_s;
+      rho = P.rho0 + d0;
+    } else {
+      rho = Real(1) + d0 + Real(kappa<L, Sc>(0, 0));
+      dx = dx + Real(kappa<L, Sc>(1, 0));
+      dy = dy + Real(kappa<L, Sc>(0, 1));
+    }
+    const Real irho = Real(1) / rho;
+    ux = dx * irho;
+    uy = dy * irho;
+    theta = Real(1);
   }
 }
 

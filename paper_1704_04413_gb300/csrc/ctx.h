@@ -23,6 +23,7 @@ struct lbm_ctx {
   double* out4 = nullptr;     // device: 4 sums, then the error word
   double* host4 = nullptr;    // pinned host copy of the same
   void* closure_buf = nullptr;  // features and outputs of the learned closure (lazily allocated)
+  void* fd_mom = nullptr;       // rho, ux, uy, theta [4][ny][nx] of the finite-difference variant
   int* dev_err = nullptr;     // device error word (bounded device waits record LBM_ETIMEOUT there)
   long long steps = 0;
   cudaStream_t st = nullptr;

@@ -29,6 +29,7 @@ struct StepGeom {
 struct CollParamsD {
   double omega, om1;  // 1 / tau, 1 - 1 / tau (order 2 of f^(1); BGK)
   double om1_3, om1_4;  // 1 - 1 / tau_n of the order-3 and order-4 coefficients of f^(1)
+  double tau, tau3;     // tau_2, tau_3 (finite-difference a1)
   int neq, nreg;
   double rho0, s, inv_s;
 };
@@ -41,6 +42,8 @@ __host__ __device__ inline CollParams<Real> cast_params(const CollParamsD& d) {
   p.om1 = Real((Sc)d.om1);
   p.om1_3 = Real((Sc)d.om1_3);
   p.om1_4 = Real((Sc)d.om1_4);
+  p.tau = Real((Sc)d.tau);
+  p.tau3 = Real((Sc)d.tau3);
   p.neq = d.neq;
   p.nreg = d.nreg;
   p.rho0 = Real((Sc)d.rho0);
@@ -121,10 +124,13 @@ struct StepBlocks {
 };
 
 // One block = STEP_BX consecutive cells of one row; the grid is 1D over (row, column block).
-template <class L, int COLL, bool THERMAL, class Real, class S>
+// FD: a1 from central differences of the moments field mom[4][ny][nx] (rho, ux, uy, theta after streaming;
+// the pass k_stream_moments writes it); neighbours follow the streaming rule (periodic wrap, or the
+// clamped edge cell on a zero-gradient axis).
+template <class L, int COLL, bool THERMAL, class Real, class S, bool FD = false>
 __global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
     k_step(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<Real> P,
-           const __grid_constant__ PullOffsets<L::Q> off) {
+           const __grid_constant__ PullOffsets<L::Q> off, const Real* __restrict__ mom = nullptr) {
   const int y = blockIdx.x / nbx;
   const int bx = blockIdx.x - y * nbx;
   const int x = bx * STEP_BX + threadIdx.x;
@@ -166,7 +172,22 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
       q[i] = (Real)ld_raw<S>(b + off.dst[i] + ((long long)ys * g.pitch + xs) * (long long)sizeof(S));
     });
   }
-  collide<L, COLL, THERMAL, Store<S>::SHIFTED>(q, P);
+  Real grad[6];
+  if constexpr (FD) {
+    const long long n = (long long)g.nx * g.ny;
+    const long long ce = (long long)y * g.nx + src_coord(x, -1, g.nx, g.bcx);
+    const long long cw = (long long)y * g.nx + src_coord(x, 1, g.nx, g.bcx);
+    const long long cn = (long long)src_coord(y, -1, g.ny, g.bcy) * g.nx + x;
+    const long long cs = (long long)src_coord(y, 1, g.ny, g.bcy) * g.nx + x;
+    const Real *mu = mom + n, *mv = mom + 2 * n, *mt = mom + 3 * n;
+    grad[0] = Real(0.5) * (mu[ce] - mu[cw]);
+    grad[1] = Real(0.5) * (mu[cn] - mu[cs]);
+    grad[2] = Real(0.5) * (mv[ce] - mv[cw]);
+    grad[3] = Real(0.5) * (mv[cn] - mv[cs]);
+    grad[4] = Real(0.5) * (mt[ce] - mt[cw]);
+    grad[5] = Real(0.5) * (mt[cn] - mt[cs]);
+  }
+  collide<L, COLL, THERMAL, Store<S>::SHIFTED, Real, false, FD>(q, P, nullptr, grad);
   char* o = reinterpret_cast<char*>(fout + cen);
   sfor<0, L::Q>([&](auto I) {
     constexpr int i = LBM_CI(I);
@@ -387,6 +408,64 @@ inline cudaError_t launch_step_t(const void* fin, void* fout, const StepGeom& g,
   return cudaGetLastError();
 }
 
+// Moments pass of the finite-difference variant: rho, ux, uy, theta of every cell after pull streaming,
+// into mom[4][ny][nx].
+template <class L, bool THERMAL, class Real, class S>
+__global__ void __launch_bounds__(128) k_stream_moments(const S* __restrict__ fin, StepGeom g, CollParams<Real> P,
+                                                        Real* __restrict__ mom) {
+  const long long n = (long long)g.nx * g.ny;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+  Real q[L::Q];
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    const int xs = src_coord(x, L::CX[i], g.nx, g.bcx);
+    const int ys = src_coord(y, L::CY[i], g.ny, g.bcy);
+    q[i] = (Real)Store<S>::ld(fin + (long long)i * g.plane + (long long)ys * g.pitch + xs);
+  });
+  Real rho, ux, uy, th;
+  cell_macro<L, THERMAL, Store<S>::SHIFTED>(q, P, rho, ux, uy, th);
+  mom[c] = rho;
+  mom[n + c] = ux;
+  mom[2 * n + c] = uy;
+  mom[3 * n + c] = th;
+}
+
+// One RR step with a1 from finite differences: the moments pass, then the step kernel reading them.
+template <class L, bool THERMAL, class Real, class S>
+inline cudaError_t launch_step_fd_t(const void* fin, void* fout, const StepGeom& g, const CollParamsD& pd,
+                                    void* mom, cudaStream_t st) {
+  const long long n = (long long)g.nx * g.ny;
+  const CollParams<Real> P = cast_params<Real>(pd);
+  k_stream_moments<L, THERMAL, Real, S><<<(unsigned)((n + 127) / 128), 128, 0, st>>>((const S*)fin, g, P,
+                                                                                     (Real*)mom);
+  PullOffsets<L::Q> off;
+  for (int i = 0; i < L::Q; ++i) {
+    off.dst[i] = (long long)i * g.plane * (long long)sizeof(S);
+    off.src[i] = off.dst[i] - ((long long)L::CY[i] * g.pitch + L::CX[i]) * (long long)sizeof(S);
+  }
+  const int nbx = (g.nx + STEP_BX - 1) / STEP_BX;
+  const long long nblocks = (long long)nbx * g.ny;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_step<L, COLL_RR, THERMAL, Real, S, true><<<(unsigned)nblocks, STEP_BX, 0, st>>>(
+      (const S*)fin, (S*)fout, g, nbx, P, off, (const Real*)mom);
+  return cudaGetLastError();
+}
+
+template <class L, bool THERMAL>
+inline cudaError_t launch_step_fd(int prec, const void* fin, void* fout, const StepGeom& g, const CollParamsD& pd,
+                                  void* mom, cudaStream_t st) {
+  switch (prec) {
+    case PREC_F64: return launch_step_fd_t<L, THERMAL, double, double>(fin, fout, g, pd, mom, st);
+    case PREC_F32: return launch_step_fd_t<L, THERMAL, float, float>(fin, fout, g, pd, mom, st);
+    case PREC_F16: return launch_step_fd_t<L, THERMAL, float, __half>(fin, fout, g, pd, mom, st);
+    case PREC_BF16: return launch_step_fd_t<L, THERMAL, float, __nv_bfloat16>(fin, fout, g, pd, mom, st);
+    case PREC_I16: return launch_step_fd_t<L, THERMAL, float, short>(fin, fout, g, pd, mom, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <class L, int COLL, bool THERMAL>
 inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const StepGeom& g,
                                     const CollParamsD& pd, cudaStream_t st) {
@@ -424,9 +503,12 @@ inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const
   return cudaErrorInvalidValue;
 }
 
+// fd_mom: moments buffer of the finite-difference variant (RR only), nullptr = a1 by projection.
 template <class L, bool THERMAL>
 inline cudaError_t launch_step_lattice(int coll, int prec, const void* fin, void* fout, const StepGeom& g,
-                                       const CollParamsD& pd, cudaStream_t st) {
+                                       const CollParamsD& pd, void* fd_mom, cudaStream_t st) {
+  if (fd_mom) return coll == COLL_RR ? launch_step_fd<L, THERMAL>(prec, fin, fout, g, pd, fd_mom, st)
+                                     : cudaErrorInvalidValue;
   switch (coll) {
     case COLL_BGK: return launch_step_prec<L, COLL_BGK, THERMAL>(prec, fin, fout, g, pd, st);
     case COLL_PR: return launch_step_prec<L, COLL_PR, THERMAL>(prec, fin, fout, g, pd, st);
@@ -441,7 +523,7 @@ inline cudaError_t launch_step_lattice(int coll, int prec, const void* fin, void
 // device error word.
 #define LBM_STEP_LAUNCHER_ARGS                                                                      \
   int coll, int prec, const void *fin, void *fout, const lbm::StepGeom &g, const lbm::CollParamsD &pd, \
-      int *err, cudaStream_t st
+      void *fd_mom, int *err, cudaStream_t st
 cudaError_t lbm_launch_step_d2q9(LBM_STEP_LAUNCHER_ARGS);
 cudaError_t lbm_launch_step_d2v17(LBM_STEP_LAUNCHER_ARGS);
 cudaError_t lbm_launch_step_d2v37(LBM_STEP_LAUNCHER_ARGS);

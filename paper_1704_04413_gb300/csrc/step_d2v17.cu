@@ -3,5 +3,5 @@
 
 cudaError_t lbm_launch_step_d2v17(LBM_STEP_LAUNCHER_ARGS) {
   (void)err;
-  return lbm::launch_step_lattice<lbm::D2V17, false>(coll, prec, fin, fout, g, pd, st);
+  return lbm::launch_step_lattice<lbm::D2V17, false>(coll, prec, fin, fout, g, pd, fd_mom, st);
 }

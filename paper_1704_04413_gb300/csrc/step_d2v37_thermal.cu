@@ -3,5 +3,5 @@
 
 cudaError_t lbm_launch_step_d2v37_thermal(LBM_STEP_LAUNCHER_ARGS) {
   (void)err;
-  return lbm::launch_step_lattice<lbm::D2V37, true>(coll, prec, fin, fout, g, pd, st);
+  return lbm::launch_step_lattice<lbm::D2V37, true>(coll, prec, fin, fout, g, pd, fd_mom, st);
 }

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 D2Q9, D2V17, D2V37 = 0, 1, 2
 BGK, PR, RR = 0, 1, 2
 PERIODIC, ZERO_GRADIENT = 0, 1
+A1_PROJECTION, A1_FINITE_DIFFERENCE = 0, 1
+A1_SOURCES = {"projection": A1_PROJECTION, "fd": A1_FINITE_DIFFERENCE}
 F64, F32, F16_SHIFT, BF16_SHIFT, I16_SHIFT = 0, 1, 2, 3, 4
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EIO = 0, -1, -2, -3, -4, -5, -6
 
@@ -40,7 +42,7 @@ class lbm_params(ctypes.Structure):
                 ("nu", ctypes.c_double), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
                 ("storage", ctypes.c_int), ("compute", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("store_scale", ctypes.c_double), ("stream", ctypes.c_void_p), ("tau3", ctypes.c_double),
-                ("tau4", ctypes.c_double)]
+                ("tau4", ctypes.c_double), ("a1_source", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -140,12 +142,13 @@ def lbm_lattice_info(lattice):
 
 def make_params(lattice="D2Q9", nx=64, ny=64, tau=0.0, nu=0.0, collision="rr", hermite_order=2, reg_order=0,
                 thermal=False, bc_x=PERIODIC, bc_y=PERIODIC, storage="f32", rho0=0.0, store_scale=0.0,
-                stream=None, tau3=0.0, tau4=0.0) -> lbm_params:
+                stream=None, tau3=0.0, tau4=0.0, a1_source=0) -> lbm_params:
     st = STORAGES.get(storage, storage)
     compute = F64 if st == F64 else F32
     return lbm_params(LATTICES.get(lattice, lattice), hermite_order, reg_order,
                       COLLISIONS.get(collision, collision), int(thermal), nx, ny, float(nu), float(tau), bc_x, bc_y,
-                      st, compute, float(rho0), float(store_scale), stream, float(tau3), float(tau4))
+                      st, compute, float(rho0), float(store_scale), stream, float(tau3), float(tau4),
+                      A1_SOURCES.get(a1_source, a1_source))
 
 
 def lbm_create(params: lbm_params):

@@ -29,7 +29,7 @@ class Ctx:
     """A library context; closes on exit."""
 
     def __init__(self, name, nx, ny, tau, coll="rr", neq=2, nreg=0, storage="f32", thermal=False,
-                 bcx=0, bcy=0, rho0=0.0, scale=0.0, tau3=0.0, tau4=0.0):
+                 bcx=0, bcy=0, rho0=0.0, scale=0.0, tau3=0.0, tau4=0.0, a1_source=0):
         m = lib()
         self.m = m
         self.name, self.nx, self.ny = name, nx, ny
@@ -37,7 +37,7 @@ class Ctx:
         self.P = perm(name)
         p = m.make_params(name, nx, ny, tau=tau, collision=coll, hermite_order=neq, reg_order=nreg,
                           thermal=thermal, bc_x=bcx, bc_y=bcy, storage=storage, rho0=rho0, store_scale=scale,
-                          stream=stream(), tau3=tau3, tau4=tau4)
+                          stream=stream(), tau3=tau3, tau4=tau4, a1_source=a1_source)
         self.ctx = m.lbm_create(p)
 
     def __enter__(self):

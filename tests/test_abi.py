@@ -67,6 +67,8 @@ def test_invalid_parameters_are_rejected_on_host(lbm):
         dict(lattice="D2Q9", tau3=0.5),                    # per-order time must exceed 1/2
         dict(lattice="D2Q9", tau4=-1.0),
         dict(lattice="D2Q9", collision="bgk", tau3=0.9),   # one time per order needs PR or RR
+        dict(lattice="D2Q9", collision="pr", a1_source=1),  # finite-difference a1 is an RR option
+        dict(lattice="D2Q9", a1_source=2),
     ]
     for kw in bad:
         kw.setdefault("tau", 0.8)
@@ -96,3 +98,5 @@ def test_batch_rejects_invalid_sets_on_host(lbm):
         lbm.lbm_batch_create([base] * 65)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_batch_create([lbm.make_params("D2Q9", 32, 32, tau=0.7, storage="f64")])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_batch_create([lbm.make_params("D2Q9", 32, 32, tau=0.7, storage="f16", a1_source=1)])

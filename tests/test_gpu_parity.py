@@ -75,6 +75,45 @@ def test_one_step_with_per_order_times_matches_oracle(name, coll, neq, nreg, the
     assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
 
 
+FD_MODES = [m for m in MODES if m[1] == "rr"]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("name,coll,neq,nreg,thermal", FD_MODES)
+def test_one_step_with_finite_difference_a1_matches_oracle(name, coll, neq, nreg, thermal, storage):
+    """RR with a1^(2) (and the thermal temperature-gradient terms) from central differences of the
+    post-streaming fields (Sec. II.E), one step on a ragged 300 x 5 grid, tau_3 != tau."""
+    nx, ny, tau = 300, 5, 0.62
+    f = oracle_state(name, nx, ny, 19, thermal)
+    op = orc.params(name, nx, ny, tau, coll, neq, nreg, thermal=thermal, tau3=0.7, a1_source=1)
+    ref = orc.step(op, f)
+    with Ctx(name, nx, ny, tau, coll, neq, nreg, storage, thermal, tau3=0.7, a1_source=1) as c:
+        c.set_oracle_f(f)
+        c.step(1)
+        got = c.get_oracle_f()
+    assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
+
+
+@pytest.mark.parametrize("name,thermal,storage", [("D2Q9", False, "f64"), ("D2V37", True, "f64"),
+                                                  ("D2V17", False, "f16")])
+def test_finite_difference_a1_with_zero_gradient_edges(name, thermal, storage):
+    """Edge gradients use the clamped neighbour (one-sided), as the streaming rule; three steps."""
+    nx, ny, tau = 67, 9, 0.7
+    f = oracle_state(name, nx, ny, 23, thermal)
+    Lt = orc.lattice(name)
+    op = orc.params(name, nx, ny, tau, "rr", Lt.nmax, thermal=thermal, bc_x=1, bc_y=1, a1_source=1)
+    ref = orc.step(op, f, 3)
+    with Ctx(name, nx, ny, tau, "rr", Lt.nmax, 0, storage, thermal, 1, 1, a1_source=1) as c:
+        c.set_oracle_f(f)
+        c.step(3)
+        got = c.get_oracle_f()
+    if storage == "f64":
+        assert max_rel(got, ref) <= 1e-12
+    else:
+        w = Lt.w[:, None, None]
+        assert np.max(np.abs(got - ref) / w) <= 2e-3 * np.abs(ref / w - 1.0).max()
+
+
 @pytest.mark.parametrize("bcx,bcy", [(1, 0), (0, 1), (1, 1)])
 @pytest.mark.parametrize("name,thermal", [("D2Q9", False), ("D2V17", False), ("D2V37", True)])
 def test_zero_gradient_boundaries_match_oracle(name, thermal, bcx, bcy):
