@@ -142,13 +142,13 @@ def shear_fields(name, L):
     return V, cs2, nu, wl.double_shear_layer(L, u0)
 
 
-def make_contexts(storage, stream, grid=GRID):
+def make_contexts(storage, stream, grid=GRID, a1_source=0):
     from paper_1704_04413_gb300 import lbm
     ctxs = []
     for name, neq in LATTICES:
         V, cs2, nu, fl = shear_fields(name, grid)
         p = lbm.make_params(name, grid, grid, nu=nu, collision="rr", hermite_order=neq, storage=storage,
-                            stream=stream)
+                            stream=stream, a1_source=a1_source)
         ctx = lbm.lbm_create(p)
         lbm.lbm_init(ctx, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
         ctxs.append((name, V, ctx, fl if grid == GRID else None))
@@ -262,6 +262,16 @@ def run_ours(args, rank, world, local_rank):
                                           "vs_f32": round(glups / per_lattice[name]["f32"]["glups"], 3)}
             lbm.lbm_destroy(ctx)
 
+    # ---- RR with a1 from finite differences (a moments pass + the step per lattice per step), FP32 ----
+    fd = {}
+    if "fd" in sec:
+        cs = make_contexts("f32", st, a1_source=1)
+        per_s, _, _ = timed_steps(cs, max(10, min(args.steps, 200)), 3, stream_t)
+        for (name, V, ctx, _), ms in zip(cs, per_s):
+            glups = ncell / (ms * 1e-3) / 1e9
+            fd[name] = {"glups": round(glups, 3), "ms": round(ms, 5),
+                        "vs_projection": round(glups / per_lattice[name]["f32"]["glups"], 3)}
+            lbm.lbm_destroy(ctx)
     # ---- above-L2 grids: consecutive steps of one 4096^2 grid (buffers 0.6-5 GB, far above the 129 MB L2) ----
     large = {}
     if "large" in sec:
@@ -291,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
                              "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
-            "per_lattice_4096": large, "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
+            "per_lattice_4096": large, "a1_finite_difference_f32": fd, "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
             "learned_closure": closure, "stability_map": stab,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
@@ -568,7 +578,7 @@ def main():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
-    ap.add_argument("--sections", default="e2e,storages,large,accuracy,batched,closure,stability,cpu",
+    ap.add_argument("--sections", default="e2e,storages,fd,large,accuracy,batched,closure,stability,cpu",
                     help="comma list of sections run after the timed headline steps (profiling runs pass "
                          "'none' to keep only the headline)")
     ap.add_argument("--closure-fine", type=int, default=2048)
