@@ -244,7 +244,8 @@ def step(p: Params3, f, n=1):
 
 def init(p: Params3, rho, u, grad=None):
     """f = f^(0) + f^(1) (Sec. III.B): rho (nz, ny, nx), u (3, nz, ny, nx); grad[a][b] = d u_a / d x_b
-    (3, 3, nz, ny, nx) or None; a1^(2)_ab = -tau rho cs^2 (d_a u_b + d_b u_a) (isothermal)."""
+    (3, 3, nz, ny, nx) or None; a1^(2)_ab = -tau rho cs^2 (d_a u_b + d_b u_a) (isothermal), continued to
+    every order of the lattice by Eq. MalaspinasRecursiveRelation (as in two dimensions)."""
     L = lattice(p.lattice)
     neq, _ = p.orders()
     shape = rho.shape
@@ -256,7 +257,8 @@ def init(p: Params3, rho, u, grad=None):
         a1 = {}
         for a, b in tuples(2):
             a1[(a, b)] = -p.tau * r * L.cs2 * (g[b, a] + g[a, b])
-        f = f + expand(p.lattice, a1, 2, 2)
+        a1_recursive(r, uu, equilibrium_coefficients(r, uu, L.nmax), a1, L.nmax)
+        f = f + expand(p.lattice, a1, 2, L.nmax)
     return f.reshape((L.V,) + shape)
 
 
