@@ -1,0 +1,425 @@
+// Kernels of the 3D lattices (Tab. II): fused pull-stream-and-collide and the field kernels (initial state,
+// moments, population planes, FP64 conservation sums).  Populations are SoA f[i][z][y][x]: rows padded to
+// 128 bytes (pitch), planes of ny rows, population blocks of nz planes.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "collide3.cuh"
+#include "step.cuh"
+
+namespace lbm {
+
+struct Geom3 {
+  long long pstride;  // elements per population block (nz * plane)
+  long long plane;    // elements per z plane (ny * pitch)
+  int pitch;          // elements per row
+  int nx, ny, nz;
+  int bc[3];          // BC_PERIODIC / BC_ZERO_GRADIENT per axis
+};
+
+template <int Q>
+struct PullOffsets3 {
+  long long src[Q];  // byte offset of the pulled source of population i from the cell's address in block 0
+  long long dst[Q];  // byte offset of population i's block
+};
+
+template <class L>
+struct Step3Blocks {
+  static constexpr int MIN = L::Q > 40 ? 1 : (L::Q > 20 ? 3 : 4);
+};
+
+// Storage formats built per lattice: all five, except D3Q103 (FP64 and FP32 only: its kernels are large
+// and each format multiplies the build time).
+template <class L>
+struct Storages3 {
+  static constexpr bool SIXTEEN_BIT = L::Q < 100;
+};
+
+// One thread per cell; a block is STEP_BX consecutive x of one (y, z) row.  Rows at least VMAX away from
+// the y and z edges (block-uniform) take one load sequence with the x wrap folded into a base pointer per
+// x-velocity; the other rows (and grids narrower than the stencil) the general path.
+template <class L, int COLL, class Real, class S>
+__global__ void __launch_bounds__(STEP_BX, Step3Blocks<L>::MIN)
+    k_step3(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, CollParams<Real> P,
+            const __grid_constant__ PullOffsets3<L::Q> off) {
+  const int row = blockIdx.x / nbx;
+  const int bx = blockIdx.x - row * nbx;
+  const int y = row % g.ny, z = row / g.ny;
+  const int x = bx * STEP_BX + threadIdx.x;
+  if (x >= g.nx) return;
+  const long long cen = (long long)z * g.plane + (long long)y * g.pitch + x;
+  Real q[L::Q];
+  if (y >= L::VMAX && y + L::VMAX < g.ny && z >= L::VMAX && z + L::VMAX < g.nz && g.nx >= L::VMAX) {
+    const char* c = reinterpret_cast<const char*>(fin + cen);
+    const char* cb[2 * L::VMAX + 1];
+    sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+      constexpr int j = LBM_CI(J);
+      constexpr int cx = j - L::VMAX;
+      if constexpr (cx == 0) {
+        cb[j] = c;
+      } else {
+        const int xs = x - cx;
+        int fix;
+        if (g.bc[0] == BC_PERIODIC)
+          fix = (xs < 0 ? g.nx : 0) - (xs >= g.nx ? g.nx : 0);
+        else
+          fix = (xs < 0 ? -xs : 0) - (xs >= g.nx ? xs - g.nx + 1 : 0);
+        cb[j] = c + (long long)fix * (long long)sizeof(S);
+      }
+    });
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      q[i] = (Real)ld_raw<S>(cb[L::CX[i] + L::VMAX] + off.src[i]);
+    });
+  } else {
+    const char* b = reinterpret_cast<const char*>(fin);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      const int xs = src_coord(x, L::CX[i], g.nx, g.bc[0]);
+      const int ys = src_coord(y, L::CY[i], g.ny, g.bc[1]);
+      const int zs = src_coord(z, L::CZ[i], g.nz, g.bc[2]);
+      q[i] = (Real)ld_raw<S>(b + off.dst[i] +
+                             ((long long)zs * g.plane + (long long)ys * g.pitch + xs) * (long long)sizeof(S));
+    });
+  }
+  collide3<L, COLL, Store<S>::SHIFTED, Real>(q, P);
+  char* o = reinterpret_cast<char*>(fout + cen);
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    Store<S>::st(reinterpret_cast<S*>(o + off.dst[i]), q[i]);
+  });
+}
+
+template <class L, int COLL, class Real, class S>
+inline cudaError_t launch_step3_t(const void* fin, void* fout, const Geom3& g, const CollParamsD& pd,
+                                  cudaStream_t st) {
+  PullOffsets3<L::Q> off;
+  for (int i = 0; i < L::Q; ++i) {
+    off.dst[i] = (long long)i * g.pstride * (long long)sizeof(S);
+    off.src[i] = off.dst[i] -
+                 ((long long)L::CZ[i] * g.plane + (long long)L::CY[i] * g.pitch + L::CX[i]) * (long long)sizeof(S);
+  }
+  const int nbx = (g.nx + STEP_BX - 1) / STEP_BX;
+  const long long nblocks = (long long)nbx * g.ny * g.nz;
+  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_step3<L, COLL, Real, S><<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
+                                                                    cast_params<Real>(pd), off);
+  return cudaGetLastError();
+}
+
+template <class L, int COLL>
+inline cudaError_t launch_step3_prec(int prec, const void* fin, void* fout, const Geom3& g, const CollParamsD& pd,
+                                     cudaStream_t st) {
+  switch (prec) {
+    case PREC_F64: return launch_step3_t<L, COLL, double, double>(fin, fout, g, pd, st);
+    case PREC_F32: return launch_step3_t<L, COLL, float, float>(fin, fout, g, pd, st);
+  }
+  if constexpr (Storages3<L>::SIXTEEN_BIT) {
+    switch (prec) {
+      case PREC_F16: return launch_step3_t<L, COLL, float, __half>(fin, fout, g, pd, st);
+      case PREC_BF16: return launch_step3_t<L, COLL, float, __nv_bfloat16>(fin, fout, g, pd, st);
+      case PREC_I16: return launch_step3_t<L, COLL, float, short>(fin, fout, g, pd, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Step launchers of one (lattice, collision) pair: one translation unit each, so that the 3D kernels
+// compile in parallel (d3_<lattice>_<collision>.cu).
+#define LBM3_STEP_SIG(name) \
+  cudaError_t name(int prec, const void* fin, void* fout, const lbm::Geom3& g, const lbm::CollParamsD& pd, \
+                   cudaStream_t st)
+
+// ---------------------------------------------------------------------------
+// Field kernels (double precision; not on the time-stepping path).  Fields are dense [nz][ny][nx].
+// ---------------------------------------------------------------------------
+constexpr int FB3 = 128;
+
+template <class L, class S, int i>
+__device__ __forceinline__ double decode3(const S* f, long long off, double rho0, double inv_s) {
+  const double q = (double)Store<S>::ld(f + off);
+  [[maybe_unused]] constexpr double w = L::W[i];
+  if constexpr (Store<S>::SHIFTED)
+    return w * (rho0 + q * inv_s);
+  else
+    return q;
+}
+
+struct Init3Params {
+  int neq;
+  double tau, rho0, s;
+};
+
+// f = f^(0) + f^(1) (Sec. III.B): f^(1) from the Chapman-Enskog a1^(2) = -tau rho cs^2 (d_a u_b + d_b u_a)
+// of the velocity gradients grad[a][b] = d u_a / d x_b ([9][cells], may be null) and its recursion to
+// every order of the lattice.
+template <class L, class S>
+__global__ void __launch_bounds__(FB3) k_init3(const double* __restrict__ rho, const double* __restrict__ u,
+                                               const double* __restrict__ grad, S* __restrict__ f, Geom3 g,
+                                               Init3Params ip) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long c = (long long)blockIdx.x * FB3 + threadIdx.x;
+  if (c >= n) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  constexpr double c2 = L::CS2;
+  const double r = rho[c];
+  const double uu[3] = {u[c], u[n + c], u[2 * n + c]};
+  double pw[3][5];
+  for (int d = 0; d < 3; ++d) {
+    pw[d][0] = 1.0;
+    for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * uu[d];
+  }
+  double b2[6] = {0, 0, 0, 0, 0, 0};
+  if (grad) {
+    const double pre = -ip.tau * r * c2;
+    auto gr = [&](int a, int b) { return grad[(long long)(3 * a + b) * n + c]; };
+    b2[0] = pre * 2.0 * gr(0, 0);
+    b2[1] = pre * 2.0 * gr(1, 1);
+    b2[2] = pre * 2.0 * gr(2, 2);
+    b2[3] = pre * (gr(0, 1) + gr(1, 0));
+    b2[4] = pre * (gr(0, 2) + gr(2, 0));
+    b2[5] = pre * (gr(1, 2) + gr(2, 1));
+  }
+  double C[5][5][5];
+  sfor<0, 5>([&](auto Aa) {
+    constexpr int a = LBM_CI(Aa);
+    sfor<0, 5>([&](auto Bb) {
+      constexpr int b = LBM_CI(Bb);
+      sfor<0, 5>([&](auto Cc) {
+        constexpr int cc = LBM_CI(Cc);
+        constexpr int nn = a + b + cc;
+        if constexpr (nn <= L::NMAX && L::keep(a, b, cc)) {
+          constexpr double sc = 1.0 / (factorial(a) * factorial(b) * factorial(cc) * ipow(c2, nn));
+          double v = (nn <= ip.neq) ? r * pw[0][a] * pw[1][b] * pw[2][cc] : 0.0;
+          if constexpr (nn >= 2) {
+            double a1 = 0.0;
+            if constexpr (a >= 2) a1 += choose2(a) * b2[0] * pw[0][a - 2] * pw[1][b] * pw[2][cc];
+            if constexpr (b >= 2) a1 += choose2(b) * b2[1] * pw[0][a] * pw[1][b - 2] * pw[2][cc];
+            if constexpr (cc >= 2) a1 += choose2(cc) * b2[2] * pw[0][a] * pw[1][b] * pw[2][cc - 2];
+            if constexpr (a >= 1 && b >= 1) a1 += a * b * b2[3] * pw[0][a - 1] * pw[1][b - 1] * pw[2][cc];
+            if constexpr (a >= 1 && cc >= 1) a1 += a * cc * b2[4] * pw[0][a - 1] * pw[1][b] * pw[2][cc - 1];
+            if constexpr (b >= 1 && cc >= 1) a1 += b * cc * b2[5] * pw[0][a] * pw[1][b - 1] * pw[2][cc - 1];
+            v += a1;
+          }
+          C[a][b][cc] = v * sc;
+        }
+      });
+    });
+  });
+  const long long o = (long long)z * g.plane + (long long)y * g.pitch + x;
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    double acc = 0.0;
+    sfor<0, 5>([&](auto Aa) {
+      constexpr int a = LBM_CI(Aa);
+      sfor<0, 5>([&](auto Bb) {
+        constexpr int b = LBM_CI(Bb);
+        sfor<0, 5>([&](auto Cc) {
+          constexpr int cc = LBM_CI(Cc);
+          if constexpr (a + b + cc <= L::NMAX && L::keep(a, b, cc)) {
+            constexpr double h = he(a, L::CX[i], c2) * he(b, L::CY[i], c2) * he(cc, L::CZ[i], c2);
+            if constexpr (h != 0.0) acc += h * C[a][b][cc];
+          }
+        });
+      });
+    });
+    // acc = f_i / w_i
+    [[maybe_unused]] constexpr double w = L::W[i];
+    double v;
+    if constexpr (Store<S>::SHIFTED)
+      v = ip.s * (acc - ip.rho0);
+    else
+      v = w * acc;
+    Store<S>::st(f + (long long)i * g.pstride + o, v);
+  });
+}
+
+// rho and u of the stored state (Sec. II.A); u is [3][cells].
+template <class L, class S>
+__global__ void __launch_bounds__(FB3) k_moments3(const S* __restrict__ f, Geom3 g, double rho0, double inv_s,
+                                                  double* __restrict__ rho, double* __restrict__ u) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long c = (long long)blockIdx.x * FB3 + threadIdx.x;
+  if (c >= n) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  const long long o = (long long)z * g.plane + (long long)y * g.pitch + x;
+  double r = 0, j[3] = {0, 0, 0};
+  sfor<0, L::Q>([&](auto I) {
+    constexpr int i = LBM_CI(I);
+    constexpr double cx = L::CX[i], cy = L::CY[i], cz = L::CZ[i];
+    const double fi = decode3<L, S, i>(f, (long long)i * g.pstride + o, rho0, inv_s);
+    r += fi;
+    j[0] += cx * fi;
+    j[1] += cy * fi;
+    j[2] += cz * fi;
+  });
+  if (rho) rho[c] = r;
+  if (u) {
+    u[c] = j[0] / r;
+    u[n + c] = j[1] / r;
+    u[2 * n + c] = j[2] / r;
+  }
+}
+
+// Decoded population i (weight wi) of every cell to dense doubles, and the inverse.
+template <class S>
+__global__ void __launch_bounds__(FB3) k_get_plane3(const S* __restrict__ f, Geom3 g, int i, double wi,
+                                                    double rho0, double inv_s, double* __restrict__ out) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long c = (long long)blockIdx.x * FB3 + threadIdx.x;
+  if (c >= n) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  const double q = (double)Store<S>::ld(f + (long long)i * g.pstride + (long long)z * g.plane +
+                                        (long long)y * g.pitch + x);
+  out[c] = Store<S>::SHIFTED ? wi * (rho0 + q * inv_s) : q;
+}
+template <class S>
+__global__ void __launch_bounds__(FB3) k_set_plane3(S* __restrict__ f, Geom3 g, int i, double wi, double rho0,
+                                                    double s, const double* __restrict__ in) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long c = (long long)blockIdx.x * FB3 + threadIdx.x;
+  if (c >= n) return;
+  const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+  const double v = Store<S>::SHIFTED ? s * (in[c] / wi - rho0) : in[c];
+  Store<S>::st(f + (long long)i * g.pstride + (long long)z * g.plane + (long long)y * g.pitch + x, v);
+}
+
+// FP64 mass and momentum: each block sums a fixed range of cells in a fixed order into partials[4][block];
+// k_sum_partials3 then adds the partials in block order (deterministic, two passes).
+template <class L, class S>
+__global__ void __launch_bounds__(FB3) k_conservation3(const S* __restrict__ f, Geom3 g, double rho0, double inv_s,
+                                                       long long per_block, double* __restrict__ partials) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  const long long c0 = (long long)blockIdx.x * per_block;
+  double acc[4] = {0, 0, 0, 0};
+  for (long long c = c0 + threadIdx.x; c < c0 + per_block && c < n; c += FB3) {
+    const int x = (int)(c % g.nx), y = (int)((c / g.nx) % g.ny), z = (int)(c / ((long long)g.nx * g.ny));
+    const long long o = (long long)z * g.plane + (long long)y * g.pitch + x;
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      constexpr double cx = L::CX[i], cy = L::CY[i], cz = L::CZ[i];
+      const double fi = decode3<L, S, i>(f, (long long)i * g.pstride + o, rho0, inv_s);
+      acc[0] += fi;
+      acc[1] += cx * fi;
+      acc[2] += cy * fi;
+      acc[3] += cz * fi;
+    });
+  }
+  __shared__ double sh[4][FB3];
+  for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = FB3 / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) partials[(long long)k * gridDim.x + blockIdx.x] = sh[k][0];
+}
+template <int K>
+__global__ void k_sum_partials3(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  double a = 0.0;
+  for (int b = 0; b < nblocks; ++b) a += partials[(long long)k * nblocks + b];
+  out[k] = a;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers of one lattice, dispatched on the storage format; the field translation unit of each lattice
+// exports them as a Lat3Ops table (api3.cu selects by lattice id).
+// ---------------------------------------------------------------------------
+struct Lat3Ops {
+  cudaError_t (*step)(int coll, int prec, const void* fin, void* fout, const Geom3& g, const CollParamsD& pd,
+                      cudaStream_t st);
+  cudaError_t (*init)(int prec, const double* rho, const double* u, const double* grad, void* f, const Geom3& g,
+                      const Init3Params& ip, cudaStream_t st);
+  cudaError_t (*moments)(int prec, const void* f, const Geom3& g, double rho0, double inv_s, double* rho,
+                         double* u, cudaStream_t st);
+  cudaError_t (*get_plane)(int prec, const void* f, const Geom3& g, int i, double rho0, double inv_s, double* out,
+                           cudaStream_t st);
+  cudaError_t (*set_plane)(int prec, void* f, const Geom3& g, int i, double rho0, double s, const double* in,
+                           cudaStream_t st);
+  cudaError_t (*conservation)(int prec, const void* f, const Geom3& g, double rho0, double inv_s, double* partials,
+                              int nblocks, double* out4, cudaStream_t st);
+  int V;
+  const int *cx, *cy, *cz;
+  const double* w;
+  double cs2;
+  int nmax, vmax;
+  int sixteen_bit;  // 16-bit storage formats built
+};
+
+template <class L, class F>
+inline cudaError_t with_storage(int prec, F&& f) {
+  switch (prec) {
+    case PREC_F64: return f(double{});
+    case PREC_F32: return f(float{});
+  }
+  if constexpr (Storages3<L>::SIXTEEN_BIT) {
+    switch (prec) {
+      case PREC_F16: return f(__half{});
+      case PREC_BF16: return f(__nv_bfloat16{});
+      case PREC_I16: return f(short{});
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+inline unsigned blocks3(const Geom3& g) {
+  return (unsigned)(((long long)g.nx * g.ny * g.nz + FB3 - 1) / FB3);
+}
+
+// Field launchers of a lattice; `step` comes from the three per-collision translation units.
+template <class L>
+struct Ops3 {
+  static cudaError_t init(int prec, const double* rho, const double* u, const double* grad, void* f,
+                          const Geom3& g, const Init3Params& ip, cudaStream_t st) {
+    return with_storage<L>(prec, [&](auto tag) {
+      using S = decltype(tag);
+      k_init3<L, S><<<blocks3(g), FB3, 0, st>>>(rho, u, grad, (S*)f, g, ip);
+      return cudaGetLastError();
+    });
+  }
+  static cudaError_t moments(int prec, const void* f, const Geom3& g, double rho0, double inv_s, double* rho,
+                             double* u, cudaStream_t st) {
+    return with_storage<L>(prec, [&](auto tag) {
+      using S = decltype(tag);
+      k_moments3<L, S><<<blocks3(g), FB3, 0, st>>>((const S*)f, g, rho0, inv_s, rho, u);
+      return cudaGetLastError();
+    });
+  }
+  static cudaError_t get_plane(int prec, const void* f, const Geom3& g, int i, double rho0, double inv_s,
+                               double* out, cudaStream_t st) {
+    return with_storage<L>(prec, [&](auto tag) {
+      using S = decltype(tag);
+      k_get_plane3<S><<<blocks3(g), FB3, 0, st>>>((const S*)f, g, i, L::W[i], rho0, inv_s, out);
+      return cudaGetLastError();
+    });
+  }
+  static cudaError_t set_plane(int prec, void* f, const Geom3& g, int i, double rho0, double s, const double* in,
+                               cudaStream_t st) {
+    return with_storage<L>(prec, [&](auto tag) {
+      using S = decltype(tag);
+      k_set_plane3<S><<<blocks3(g), FB3, 0, st>>>((S*)f, g, i, L::W[i], rho0, s, in);
+      return cudaGetLastError();
+    });
+  }
+  static cudaError_t conservation(int prec, const void* f, const Geom3& g, double rho0, double inv_s,
+                                  double* partials, int nblocks, double* out4, cudaStream_t st) {
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long per_block = (n + nblocks - 1) / nblocks;
+    return with_storage<L>(prec, [&](auto tag) {
+      using S = decltype(tag);
+      k_conservation3<L, S><<<nblocks, FB3, 0, st>>>((const S*)f, g, rho0, inv_s, per_block, partials);
+      k_sum_partials3<4><<<1, 32, 0, st>>>(partials, nblocks, out4);
+      return cudaGetLastError();
+    });
+  }
+  static Lat3Ops table(decltype(Lat3Ops::step) step) {
+    return Lat3Ops{step, init, moments, get_plane, set_plane, conservation, L::Q, L::CX, L::CY, L::CZ, L::W,
+                   L::CS2, L::NMAX, L::VMAX, Storages3<L>::SIXTEEN_BIT ? 1 : 0};
+  }
+};
+
+}  // namespace lbm

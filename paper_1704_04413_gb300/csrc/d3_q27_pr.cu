@@ -1,0 +1,6 @@
+// D3Q27 (Tab. II) step kernels with the PR collision.
+#include "d3.cuh"
+
+LBM3_STEP_SIG(lbm3_step_d3q27_pr) {
+  return lbm::launch_step3_prec<lbm::D3Q27, lbm::COLL_PR>(prec, fin, fout, g, pd, st);
+}

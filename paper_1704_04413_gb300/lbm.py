@@ -382,3 +382,127 @@ def lbm_step_closure(ctx, cl, u0, n=1):
 
 def lbm_closure_apply(ctx, y, u0):
     return _check(_cl().lbm_closure_apply(ctx, _dptr(y), float(u0)), ctx, "lbm_closure_apply")
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional lattices (include/lbm3.h)
+# ---------------------------------------------------------------------------
+D3Q19, D3Q27, D3V39, D3Q103 = 10, 11, 12, 13
+LATTICES3 = {"D3Q19": D3Q19, "D3Q27": D3Q27, "D3V39": D3V39, "D3Q103": D3Q103}
+EXPORTED3 = ["lbm3_lattice_info", "lbm3_create", "lbm3_destroy", "lbm3_init", "lbm3_step", "lbm3_moments",
+             "lbm3_conservation", "lbm3_get_populations", "lbm3_set_populations", "lbm3_tau"]
+
+
+class lbm3_params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("hermite_order", ctypes.c_int), ("reg_order", ctypes.c_int),
+                ("collision", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nu", ctypes.c_double), ("tau", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("bc_z", ctypes.c_int), ("storage", ctypes.c_int), ("compute", ctypes.c_int),
+                ("rho0", ctypes.c_double), ("store_scale", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+_lbm3_ready = False
+
+
+def _l3():
+    global _lbm3_ready
+    lib = load()
+    if not _lbm3_ready:
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "lbm3_lattice_info": (ctypes.c_int, [ctypes.c_int, ip, ip, ip, ip, dp, dp]),
+            "lbm3_create": (ctypes.c_int, [ctypes.POINTER(lbm3_params), ctypes.POINTER(vp)]),
+            "lbm3_destroy": (None, [vp]),
+            "lbm3_init": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int]),
+            "lbm3_step": (ctypes.c_int, [vp, ctypes.c_int]),
+            "lbm3_moments": (ctypes.c_int, [vp, vp, vp, ctypes.c_int]),
+            "lbm3_conservation": (ctypes.c_int, [vp, dp]),
+            "lbm3_get_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+            "lbm3_set_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+            "lbm3_tau": (ctypes.c_double, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lbm3_ready = True
+    return lib
+
+
+def lbm3_lattice_info(lattice):
+    """(V, cx, cy, cz, w, cs2) of a 3D lattice, in the library's velocity order."""
+    V = ctypes.c_int()
+    cx, cy, cz = (np.zeros(128, dtype=np.int32) for _ in range(3))
+    w = np.zeros(128)
+    cs2 = ctypes.c_double()
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    _check(_l3().lbm3_lattice_info(LATTICES3.get(lattice, lattice), ctypes.byref(V), ip(cx), ip(cy), ip(cz),
+                                   w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cs2)),
+           what="lbm3_lattice_info")
+    n = V.value
+    return n, cx[:n].copy(), cy[:n].copy(), cz[:n].copy(), w[:n].copy(), cs2.value
+
+
+def make_params3(lattice="D3Q19", nx=16, ny=16, nz=16, tau=0.0, nu=0.0, collision="rr", hermite_order=2,
+                 reg_order=0, bc=(PERIODIC, PERIODIC, PERIODIC), storage="f32", rho0=0.0, store_scale=0.0,
+                 stream=None) -> lbm3_params:
+    st = STORAGES.get(storage, storage)
+    compute = F64 if st == F64 else F32
+    return lbm3_params(LATTICES3.get(lattice, lattice), hermite_order, reg_order,
+                       COLLISIONS.get(collision, collision), nx, ny, nz, float(nu), float(tau), bc[0], bc[1], bc[2],
+                       st, compute, float(rho0), float(store_scale), stream)
+
+
+def lbm3_create(p: lbm3_params):
+    c = ctypes.c_void_p()
+    _check(_l3().lbm3_create(ctypes.byref(p), ctypes.byref(c)), what="lbm3_create")
+    return c
+
+
+def lbm3_destroy(ctx) -> None:
+    _l3().lbm3_destroy(ctx)
+
+
+def _ptrs(*arrays):
+    ptrs = [_ptr(a) for a in arrays]
+    flags = {p[1] for p in ptrs if p[1] is not None}
+    if len(flags) != 1:
+        raise TypeError("mix of host and device arrays")
+    return [p[0] for p in ptrs], flags.pop()
+
+
+def lbm3_init(ctx, rho, u, grad=None):
+    """rho [nz][ny][nx], u [3][nz][ny][nx], grad [9][nz][ny][nx] (component 3a + b = d u_a / d x_b) or None."""
+    (pr, pu, pg), dev = _ptrs(rho, u, grad)
+    return _check(_l3().lbm3_init(ctx, pr, pu, pg, dev), what="lbm3_init")
+
+
+def lbm3_step(ctx, n=1):
+    return _check(_l3().lbm3_step(ctx, int(n)), what="lbm3_step")
+
+
+def lbm3_moments(ctx, rho=None, u=None):
+    (pr, pu), dev = _ptrs(rho, u)
+    return _check(_l3().lbm3_moments(ctx, pr, pu, dev), what="lbm3_moments")
+
+
+def lbm3_conservation(ctx, raise_unstable=True) -> np.ndarray:
+    out = np.zeros(4)
+    rc = _l3().lbm3_conservation(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != EUNSTABLE or raise_unstable:
+        _check(rc, what="lbm3_conservation")
+    return out
+
+
+def lbm3_get_populations(ctx, f):
+    (p,), dev = _ptrs(f)
+    return _check(_l3().lbm3_get_populations(ctx, p, dev), what="lbm3_get_populations")
+
+
+def lbm3_set_populations(ctx, f):
+    (p,), dev = _ptrs(f)
+    return _check(_l3().lbm3_set_populations(ctx, p, dev), what="lbm3_set_populations")
+
+
+def lbm3_tau(ctx) -> float:
+    return _l3().lbm3_tau(ctx)

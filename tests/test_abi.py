@@ -27,7 +27,7 @@ def declared_functions():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", txt))
+            names |= set(re.findall(r"\b(lbm3?_\w+)\s*\(", txt))
     return names
 
 
@@ -38,6 +38,7 @@ def test_every_declared_symbol_is_exported(lbm):
     for name in decl:
         assert hasattr(lib, name), name
     assert set(lbm.EXPORTED) <= decl
+    assert set(lbm.EXPORTED3) <= decl
 
 
 @pytest.mark.parametrize("name", ["D2Q9", "D2V17", "D2V37"])
@@ -100,3 +101,27 @@ def test_batch_rejects_invalid_sets_on_host(lbm):
         lbm.lbm_batch_create([lbm.make_params("D2Q9", 32, 32, tau=0.7, storage="f64")])
     with pytest.raises(lbm.LbmError):
         lbm.lbm_batch_create([lbm.make_params("D2Q9", 32, 32, tau=0.7, storage="f16", a1_source=1)])
+
+
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27", "D3V39", "D3Q103"])
+def test_3d_lattice_info_matches_oracle(lbm, name):
+    from oracle import lbm3d
+    V, cx, cy, cz, w, cs2 = lbm.lbm3_lattice_info(name)
+    L = lbm3d.lattice(name)
+    assert V == L.V and abs(cs2 - L.cs2) < 1e-15
+    lib = {(a, b, c): ww for a, b, c, ww in zip(cx, cy, cz, w)}
+    ora = {tuple(int(v) for v in xi): ww for xi, ww in zip(L.xi, L.w)}
+    assert set(lib) == set(ora)
+    for k in lib:
+        assert abs(lib[k] - ora[k]) < 1e-16
+
+
+def test_3d_invalid_parameters_are_rejected_on_host(lbm):
+    bad = [dict(lattice="D3Q19", hermite_order=4), dict(lattice="D3Q27", reg_order=7),
+           dict(lattice="D3Q19", tau=0.5), dict(lattice="D3Q19", nz=0), dict(lattice="D3Q19", bc=(0, 0, 3)),
+           dict(lattice="D3Q103", storage="bf16"), dict(lattice=42)]
+    for kw in bad:
+        kw.setdefault("tau", 0.8)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm3_create(lbm.make_params3(**kw))
+        assert e.value.code == lbm.EINVAL, kw
