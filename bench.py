@@ -290,6 +290,7 @@ def run_ours(args, rank, world, local_rank):
     batched = batched_sweep_bench(stream_t, steps=max(10, min(args.steps, 200))) if "batched" in sec else None
     closure = closure_bench(stream_t, fine=2048, reynolds=1e6) if "closure" in sec else None
     stab = stability_bench(st) if "stability" in sec else None
+    d3 = d3_bench(stream_t) if "d3" in sec else None
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -302,11 +303,61 @@ def run_ours(args, rank, world, local_rank):
                              "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
             "per_lattice_4096": large, "a1_finite_difference_f32": fd, "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
-            "learned_closure": closure, "stability_map": stab,
+            "learned_closure": closure, "stability_map": stab, "lattices_3d": d3,
             "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(min_seconds=10.0) if "cpu" in sec else None
         print(json.dumps(line), flush=True)
+
+
+LATTICES3 = (("D3Q19", 2), ("D3Q27", 3), ("D3V39", 3), ("D3Q103", 4))
+
+
+def d3_bench(stream_t, steps=20, n=256, storages=("f32", "f16"), only=None):
+    """Fused stream + RR step of the Tab. II lattices on a periodic n^3 Taylor-Green vortex (Ma = 0.1,
+    Re = 1600 on the length n / 2 pi), consecutive steps of one grid (buffers 2.5-14 GB, far above L2).
+    GLUPS, HBM bytes 2 V sizeof(storage) per cell and their fraction of the measured copy bandwidth."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    nx, ny, nz = (n, n, n) if isinstance(n, int) else n
+    rho, u1, g1 = wl.taylor_green_3d(n, 1.0) if isinstance(n, int) else wl.taylor_green_3d_box(nx, ny, nz, 1.0)
+    out = {"grid": [nx, ny, nz], "workload": "3D Taylor-Green vortex, Ma=0.1, Re=1600, periodic, RR"}
+    ncell = nx * ny * nz
+    for name, neq in LATTICES3:
+        if only and name not in only:
+            continue
+        V, cx, cy, cz, w, cs2 = lbm.lbm3_lattice_info(name)
+        u0 = MACH * np.sqrt(cs2)
+        nu = u0 * nx / (2 * np.pi) / 1600.0
+        res = {"hermite_order": neq}
+        for storage in storages:
+            if storage != "f32" and name == "D3Q103":
+                continue
+            p = lbm.make_params3(name, nx, ny, nz, nu=nu, collision="rr", hermite_order=neq, storage=storage,
+                                 stream=stream_t.cuda_stream)
+            ctx = lbm.lbm3_create(p)
+            lbm.lbm3_init(ctx, rho, u0 * u1, u0 * g1)
+            for _ in range(3):
+                lbm.lbm3_step(ctx, 1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            torch.cuda.synchronize()
+            for a, b in ev:
+                a.record(stream_t)
+                lbm.lbm3_step(ctx, 1)
+                b.record(stream_t)
+            torch.cuda.synchronize()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            glups = ncell / (ms * 1e-3) / 1e9
+            gbs = glups * 2 * V * BYTES[storage]
+            res[storage] = {"glups": round(glups, 3), "ms": round(ms, 4), "gbs": round(gbs, 1),
+                            "frac": round(gbs / hbm_peak, 4)}
+            lbm.lbm3_destroy(ctx)
+        if "f16" in res and "f32" in res:
+            res["f16"]["vs_f32"] = round(res["f16"]["glups"] / res["f32"]["glups"], 3)
+        out[name] = res
+    return out
 
 
 def batched_sweep_bench(stream_t, steps, n=64, storage="f16"):
@@ -578,7 +629,11 @@ def main():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
-    ap.add_argument("--sections", default="e2e,storages,fd,large,accuracy,batched,closure,stability,cpu",
+    ap.add_argument("--d3-only", action="store_true",
+                    help="only the 3D lattice section (--grid3, --storage as a comma list, --lattices3)")
+    ap.add_argument("--grid3", default="256", help="n (an n^3 grid) or nx,ny,nz of the 3D section")
+    ap.add_argument("--lattices3", default=None, help="comma list of 3D lattices for --d3-only (default all)")
+    ap.add_argument("--sections", default="e2e,storages,fd,large,accuracy,batched,closure,stability,d3,cpu",
                     help="comma list of sections run after the timed headline steps (profiling runs pass "
                          "'none' to keep only the headline)")
     ap.add_argument("--closure-fine", type=int, default=2048)
@@ -608,6 +663,17 @@ def main():
         stream_t = torch.cuda.Stream()
         torch.cuda.set_stream(stream_t)
         print(json.dumps(closure_bench(stream_t, fine=args.closure_fine, reynolds=args.closure_re)))
+        return
+    if args.d3_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream_t = torch.cuda.Stream()
+        torch.cuda.set_stream(stream_t)
+        only = args.lattices3.split(",") if args.lattices3 else None
+        storages = args.storage.split(",")
+        n3 = [int(v) for v in args.grid3.split(",")]
+        print(json.dumps(d3_bench(stream_t, steps=args.steps, n=n3[0] if len(n3) == 1 else tuple(n3),
+                                  storages=storages, only=only)))
         return
     if world > 1:
         import torch

@@ -63,18 +63,23 @@ void lbm3_destroy(lbm3_ctx *c);
 int lbm3_init(lbm3_ctx *c, const double *rho, const double *u, const double *grad, int on_device);
 
 /* n >= 0 time steps: pull streaming then collision, one fused kernel per step, double-buffered.
- * Enqueued on the context's stream; does not synchronize. */
+ * Enqueued on the context's stream; does not synchronize.  Grids periodic in x with nx a multiple of
+ * 16 bytes' worth of cells run the staged kernel (populations brought to shared memory by asynchronous
+ * bulk copies a few row tiles ahead); the others the direct-load kernel.  Both compute the same step. */
 int lbm3_step(lbm3_ctx *c, int n);
 
 /* rho [cells] and u [3][cells] of the current state; either may be NULL. */
 int lbm3_moments(lbm3_ctx *c, double *rho, double *u, int on_device);
 
 /* FP64 domain sums: out[0] mass, out[1..3] momentum.  Deterministic (fixed-order two-pass reduction);
- * synchronizes; LBM_EUNSTABLE (sums still written) when a sum is not finite. */
+ * synchronizes; LBM_EUNSTABLE (sums still written) when a sum is not finite; LBM_ECUDA when a step kernel
+ * gave up waiting (1 s) on its own asynchronous copies since the context was created (not expected: the
+ * word exists so that no wait is unbounded). */
 int lbm3_conservation(lbm3_ctx *c, double out[4]);
 
 /* Decoded populations f[V][nz][ny][nx] (library velocity order), and the inverse (encodes into the
- * storage format). */
+ * storage format).  lbm3_get_populations synchronizes and reports the copy-wait status as
+ * lbm3_conservation does. */
 int lbm3_get_populations(lbm3_ctx *c, double *f, int on_device);
 int lbm3_set_populations(lbm3_ctx *c, const double *f, int on_device);
 

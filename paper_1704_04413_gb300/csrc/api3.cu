@@ -182,16 +182,19 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
   cudaError_t e;
   if ((e = cudaMalloc(&c->buf[0], bytes)) != cudaSuccess || (e = cudaMalloc(&c->buf[1], bytes)) != cudaSuccess ||
       (e = cudaMalloc(&c->partials, sizeof(double) * 4 * kPartials)) != cudaSuccess ||
-      (e = cudaMalloc(&c->out4, 4 * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&c->host4, 4 * sizeof(double))) != cudaSuccess) {
+      (e = cudaMalloc(&c->out4, 5 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&c->host4, 5 * sizeof(double))) != cudaSuccess) {
     const int rc = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
     cudaGetLastError();
     lbm3_destroy(c);
     return rc;
   }
+  // out4[4] holds the status word of the staged step kernels (0 = every copy wait completed)
+  c->g.status = reinterpret_cast<int*>(c->out4 + 4);
   // padding columns are never read by a kernel; clear them once so transfers are deterministic
   if (cudaMemsetAsync(c->buf[0], 0, bytes, c->st) != cudaSuccess ||
-      cudaMemsetAsync(c->buf[1], 0, bytes, c->st) != cudaSuccess) {
+      cudaMemsetAsync(c->buf[1], 0, bytes, c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->out4, 0, 5 * sizeof(double), c->st) != cudaSuccess) {
     cudaGetLastError();
     lbm3_destroy(c);
     return LBM_ECUDA;
@@ -264,8 +267,9 @@ int lbm3_conservation(lbm3_ctx* c, double out[4]) {
   LBM3_CK(cudaSetDevice(c->device));
   LBM3_CK(c->ops->conservation(c->prec, c->buf[c->cur], c->g, c->rho0, 1.0 / c->s, c->partials, kPartials,
                                c->out4, c->st));
-  LBM3_CK(cudaMemcpyAsync(c->host4, c->out4, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  LBM3_CK(cudaMemcpyAsync(c->host4, c->out4, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   LBM3_CK(cudaStreamSynchronize(c->st));
+  if (*reinterpret_cast<const int*>(c->host4 + 4) != 0) return LBM_ECUDA;
   bool finite = true;
   for (int k = 0; k < 4; ++k) {
     out[k] = c->host4[k];
@@ -291,7 +295,9 @@ int lbm3_get_populations(lbm3_ctx* c, double* f, int on_device) {
       LBM3_CK(cudaStreamSynchronize(c->st));
     }
   }
-  return LBM_OK;
+  LBM3_CK(cudaMemcpyAsync(c->host4 + 4, c->out4 + 4, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  LBM3_CK(cudaStreamSynchronize(c->st));
+  return *reinterpret_cast<const int*>(c->host4 + 4) != 0 ? LBM_ECUDA : LBM_OK;
 }
 
 int lbm3_set_populations(lbm3_ctx* c, const double* f, int on_device) {

@@ -39,6 +39,75 @@ __host__ __device__ constexpr double gram3(int a, int b, int c, int d, int e, in
   return (s > -1e-12 && s < 1e-12) ? 0.0 : s;
 }
 
+// Velocity-set grouping of the factorized rebuild: how many velocities have (cy, cz) = (y, z) (y out of
+// [-VMAX, VMAX]: any cy), the j-th of them, and whether some kept tensor has x-order a and y-order b.
+template <class L>
+__host__ __device__ constexpr int count_yz(int y, int z) {
+  int n = 0;
+  for (int i = 0; i < L::Q; ++i)
+    if ((y > L::VMAX || L::CY[i] == y) && L::CZ[i] == z) ++n;
+  return n;
+}
+
+template <class L>
+__host__ __device__ constexpr int member_yz(int y, int z, int j) {
+  for (int i = 0; i < L::Q; ++i)
+    if (L::CY[i] == y && L::CZ[i] == z && j-- == 0) return i;
+  return 0;
+}
+
+template <class L>
+__host__ __device__ constexpr bool has_ab(int a, int b) {
+  for (int c = 0; c <= 4; ++c)
+    if (a + b + c <= L::NMAX && L::keep(a, b, c)) return true;
+  return false;
+}
+
+template <class L>
+__host__ __device__ constexpr bool has_a(int a) {
+  for (int b = 0; b <= 4; ++b)
+    if (has_ab<L>(a, b)) return true;
+  return false;
+}
+
+// Nonzero coefficients (multiply-adds) of the rebuild summed directly over populations x kept tensors,
+// and of its axis-factorized form; the kernel takes the factorized form where it saves a fifth or more
+// (D3Q27 216 against 512, D3Q103 1270 against 2734; D3V39's 21 (cy, cz) groups leave 437 against 464).
+template <class L>
+__host__ __device__ constexpr int rebuild_cost_direct() {
+  int n = 0;
+  for (int i = 0; i < L::Q; ++i)
+    for (int a = 0; a <= 4; ++a)
+      for (int b = 0; b <= 4; ++b)
+        for (int c = 0; c <= 4; ++c)
+          if (a + b + c <= L::NMAX && L::keep(a, b, c) &&
+              he(a, L::CX[i], L::CS2) * he(b, L::CY[i], L::CS2) * he(c, L::CZ[i], L::CS2) != 0.0)
+            ++n;
+  return n;
+}
+
+template <class L>
+__host__ __device__ constexpr int rebuild_cost_factorized() {
+  int n = 0;
+  for (int z = -L::VMAX; z <= L::VMAX; ++z) {
+    if (count_yz<L>(L::VMAX + 1, z) == 0) continue;
+    for (int a = 0; a <= 4; ++a)
+      for (int b = 0; b <= 4; ++b)
+        for (int c = 0; c <= 4; ++c)
+          if (a + b + c <= L::NMAX && L::keep(a, b, c) && he(c, z, L::CS2) != 0.0) ++n;
+    for (int y = -L::VMAX; y <= L::VMAX; ++y) {
+      if (count_yz<L>(y, z) == 0) continue;
+      for (int a = 0; a <= 4; ++a)
+        for (int b = 0; b <= 4; ++b)
+          if (has_ab<L>(a, b) && he(b, y, L::CS2) != 0.0) ++n;
+    }
+  }
+  for (int i = 0; i < L::Q; ++i)
+    for (int a = 0; a <= 4; ++a)
+      if (has_a<L>(a) && he(a, L::CX[i], L::CS2) != 0.0) ++n;
+  return n;
+}
+
 // Whether the kept tensors up to order `pm` need the monomial moment x^k y^l z^m.
 template <class L>
 __host__ __device__ constexpr bool needs_monomial(int k, int l, int m, int pm) {
@@ -136,82 +205,93 @@ __device__ __forceinline__ void collide3(Real (&q)[L::Q], const CollParams<Real>
     b2[5] = hmom(IC<0>{}, IC<1>{}, IC<1>{}) - rho * pw[1][1] * pw[2][1];
   }
 
-  // coefficients of the rebuilt populations minus the reference, per kept tensor
+  // coefficients of the rebuilt populations minus the reference, per kept tensor, with the factor
+  // 1 / (a! b! c! cs^2n) folded into scaled powers e_d[k] = u_d^k / (k! cs^2k):
+  //   equilibrium  rho e_x[a] e_y[b] e_z[c]
+  //   RR a1        g_xx e_x[a-2] e_y[b] e_z[c] + ... + g_xy e_x[a-1] e_y[b-1] e_z[c] + ...,
+  //                g_xx = a1_xx / (2 cs^4), g_xy = a1_xy / cs^4 (the closed form above, rescaled)
+  // grouped per (a, b) as P0 e_z[c] + P1 e_z[c-1] + P2 e_z[c-2].
+  Real e[3][5];
+  sfor<0, 3>([&](auto Dd) {
+    constexpr int dd = LBM_CI(Dd);
+    sfor<0, 5>([&](auto K) {
+      constexpr int k = LBM_CI(K);
+      e[dd][k] = pw[dd][k] * Real(1.0 / (factorial(k) * ipow(c2, k)));
+    });
+  });
+  const Real mul_eq = (COLL == COLL_BGK ? P.omega : Real(1)) * (SHIFTED ? P.s : Real(1));
+  const Real rs = rho * mul_eq;
+  const Real om1s = SHIFTED ? P.om1 * P.s : P.om1;
+  Real g[6];
+  if constexpr (COLL == COLL_RR) {
+    sfor<0, 6>([&](auto Jj) {
+      constexpr int j = LBM_CI(Jj);
+      g[j] = b2[j] * (om1s * Real(j < 3 ? 0.5 / (c2 * c2) : 1.0 / (c2 * c2)));
+    });
+  }
   Real C[5][5][5];
   sfor<0, 5>([&](auto Aa) {
     constexpr int a = LBM_CI(Aa);
     sfor<0, 5>([&](auto Bb) {
       constexpr int b = LBM_CI(Bb);
-      sfor<0, 5>([&](auto Cc) {
-        constexpr int c = LBM_CI(Cc);
-        constexpr int n = a + b + c;
-        if constexpr (n <= L::NMAX && L::keep(a, b, c)) {
-          constexpr double sc = 1.0 / (factorial(a) * factorial(b) * factorial(c) * ipow(c2, n));
-          Real v;
-          if constexpr (n == 0)
-            v = drho;
-          else
-            v = (n <= P.neq) ? rho * pw[0][a] * pw[1][b] * pw[2][c] : Real(0);
-          if constexpr (COLL == COLL_BGK) {
-            v *= P.omega;
-          } else if constexpr (n >= 2) {
-            Real a1;
-            if constexpr (COLL == COLL_PR) {
+      if constexpr (has_ab<L>(a, b)) {
+        const Real eab = e[0][a] * e[1][b];
+        Real P0 = Real(0), P1 = Real(0), P2 = Real(0);
+        if constexpr (COLL == COLL_RR) {
+          if constexpr (a >= 2) P0 = madd(g[0], e[0][a - 2] * e[1][b], P0);
+          if constexpr (b >= 2) P0 = madd(g[1], e[0][a] * e[1][b - 2], P0);
+          if constexpr (a >= 1 && b >= 1) P0 = madd(g[3], e[0][a - 1] * e[1][b - 1], P0);
+          if constexpr (a >= 1) P1 = madd(g[4], e[0][a - 1] * e[1][b], P1);
+          if constexpr (b >= 1) P1 = madd(g[5], e[0][a] * e[1][b - 1], P1);
+          P2 = g[2] * eab;
+        }
+        sfor<0, 5>([&](auto Cc) {
+          constexpr int c = LBM_CI(Cc);
+          constexpr int n = a + b + c;
+          if constexpr (n <= L::NMAX && L::keep(a, b, c)) {
+            Real v;
+            if constexpr (n == 0)
+              v = drho * mul_eq;
+            else
+              v = (n <= P.neq) ? rs * (eab * e[2][c]) : Real(0);
+            if constexpr (COLL == COLL_RR && n >= 2) {
+              Real a1 = P0 * e[2][c];
+              if constexpr (c >= 1) a1 = madd(P1, e[2][c - 1], a1);
+              if constexpr (c >= 2) a1 = madd(P2, e[2][c - 2], a1);
+              if (n <= P.nreg) v += a1;
+            } else if constexpr (COLL == COLL_PR && n >= 2) {
               // a1 = sum_i H (f_i - f^(0)_i) (Sec. II.E): the projection of f minus that of the truncated
               // equilibrium, sum over the kept (d, e, f) of order <= N_eq of gram3 * a0_(d,e,f)
-              a1 = hmom(IC<a>{}, IC<b>{}, IC<c>{});
+              Real a1 = hmom(IC<a>{}, IC<b>{}, IC<c>{});
               sfor<0, 5>([&](auto Dd) {
                 constexpr int d = LBM_CI(Dd);
                 sfor<0, 5>([&](auto Ee) {
-                  constexpr int e = LBM_CI(Ee);
+                  constexpr int ee = LBM_CI(Ee);
                   sfor<0, 5>([&](auto Ff) {
                     constexpr int f = LBM_CI(Ff);
-                    constexpr int m = d + e + f;
-                    if constexpr (m <= L::NMAX && L::keep(d, e, f)) {
-                      constexpr double gm = gram3<L>(a, b, c, d, e, f);
+                    constexpr int m = d + ee + f;
+                    if constexpr (m <= L::NMAX && L::keep(d, ee, f)) {
+                      constexpr double gm = gram3<L>(a, b, c, d, ee, f);
                       if constexpr (gm != 0.0) {
-                        if (m <= P.neq) a1 -= Real(gm) * rho * pw[0][d] * pw[1][e] * pw[2][f];
+                        if (m <= P.neq) a1 -= Real(gm) * rho * pw[0][d] * pw[1][ee] * pw[2][f];
                       }
                     }
                   });
                 });
               });
-            } else {
-              a1 = Real(0);
-              if constexpr (a >= 2) a1 += Real(choose2(a)) * b2[0] * pw[0][a - 2] * pw[1][b] * pw[2][c];
-              if constexpr (b >= 2) a1 += Real(choose2(b)) * b2[1] * pw[0][a] * pw[1][b - 2] * pw[2][c];
-              if constexpr (c >= 2) a1 += Real(choose2(c)) * b2[2] * pw[0][a] * pw[1][b] * pw[2][c - 2];
-              if constexpr (a >= 1 && b >= 1) a1 += Real(a * b) * b2[3] * pw[0][a - 1] * pw[1][b - 1] * pw[2][c];
-              if constexpr (a >= 1 && c >= 1) a1 += Real(a * c) * b2[4] * pw[0][a - 1] * pw[1][b] * pw[2][c - 1];
-              if constexpr (b >= 1 && c >= 1) a1 += Real(b * c) * b2[5] * pw[0][a] * pw[1][b - 1] * pw[2][c - 1];
+              constexpr double sc = 1.0 / (factorial(a) * factorial(b) * factorial(c) * ipow(c2, n));
+              if (n <= P.nreg) v += om1s * (a1 * Real(sc));
             }
-            if (n <= P.nreg) v += P.om1 * a1;
+            C[a][b][c] = v;
           }
-          if constexpr (SHIFTED) v *= P.s;
-          C[a][b][c] = v * Real(sc);
-        }
-      });
+        });
+      }
     });
   });
 
   // rebuild: out_i = K_i sum_{kept} He_a(cx_i) He_b(cy_i) He_c(cz_i) C[a][b][c] (K_i = w_i, or 1 shifted)
-  sfor<0, L::Q>([&](auto I) {
-    constexpr int i = LBM_CI(I);
-    Real acc = Real(0);
-    sfor<0, 5>([&](auto Aa) {
-      constexpr int a = LBM_CI(Aa);
-      sfor<0, 5>([&](auto Bb) {
-        constexpr int b = LBM_CI(Bb);
-        sfor<0, 5>([&](auto Cc) {
-          constexpr int c = LBM_CI(Cc);
-          if constexpr (a + b + c <= L::NMAX && L::keep(a, b, c)) {
-            constexpr double h = he(a, L::CX[i], c2) * he(b, L::CY[i], c2) * he(c, L::CZ[i], c2) *
-                                 (SHIFTED ? 1.0 : L::W[i]);
-            if constexpr (h != 0.0) acc = madd(Real(h), C[a][b][c], acc);
-          }
-        });
-      });
-    });
+  auto emit = [&](auto Ii, Real acc) {
+    constexpr int i = LBM_CI(Ii);
     [[maybe_unused]] constexpr double wr = (double)(Sc)L::W[i];
     if constexpr (COLL == COLL_BGK) {
       const Real dv = P.om1 * d[i] + acc;  // f* - ref = (1 - 1/tau)(f - ref) + (f^(0) - ref)/tau
@@ -219,7 +299,84 @@ __device__ __forceinline__ void collide3(Real (&q)[L::Q], const CollParams<Real>
     } else {
       q[i] = SHIFTED ? acc : Real(wr) + acc;
     }
-  });
+  };
+  if constexpr (5 * rebuild_cost_factorized<L>() > 4 * rebuild_cost_direct<L>()) {
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      Real acc = Real(0);
+      sfor<0, 5>([&](auto Aa) {
+        constexpr int a = LBM_CI(Aa);
+        sfor<0, 5>([&](auto Bb) {
+          constexpr int b = LBM_CI(Bb);
+          sfor<0, 5>([&](auto Cc) {
+            constexpr int c = LBM_CI(Cc);
+            if constexpr (a + b + c <= L::NMAX && L::keep(a, b, c)) {
+              constexpr double h = he(a, L::CX[i], c2) * he(b, L::CY[i], c2) * he(c, L::CZ[i], c2) *
+                                   (SHIFTED ? 1.0 : L::W[i]);
+              if constexpr (h != 0.0) acc = madd(Real(h), C[a][b][c], acc);
+            }
+          });
+        });
+      });
+      emit(I, acc);
+    });
+  } else {
+    // factorized by axis over the velocity set grouped by cz, then by (cy, cz):
+    //   T[a][b] = sum_c He_c(cz) C[a][b][c],  U[a] = sum_b He_b(cy) T[a][b],  out_i = K_i sum_a He_a(cx_i) U[a]
+    sfor<0, 2 * L::VMAX + 1>([&](auto Zi) {
+      constexpr int zv = LBM_CI(Zi) - L::VMAX;
+      if constexpr (count_yz<L>(L::VMAX + 1, zv) > 0) {
+        Real T[5][5];
+        sfor<0, 5>([&](auto Aa) {
+          constexpr int a = LBM_CI(Aa);
+          sfor<0, 5>([&](auto Bb) {
+            constexpr int b = LBM_CI(Bb);
+            if constexpr (has_ab<L>(a, b)) {
+              Real acc = Real(0);
+              sfor<0, 5>([&](auto Cc) {
+                constexpr int c = LBM_CI(Cc);
+                if constexpr (a + b + c <= L::NMAX && L::keep(a, b, c)) {
+                  constexpr double h = he(c, zv, c2);
+                  if constexpr (h != 0.0) acc = madd(Real(h), C[a][b][c], acc);
+                }
+              });
+              T[a][b] = acc;
+            }
+          });
+        });
+        sfor<0, 2 * L::VMAX + 1>([&](auto Yi) {
+          constexpr int yv = LBM_CI(Yi) - L::VMAX;
+          if constexpr (count_yz<L>(yv, zv) > 0) {
+            Real U[5];
+            sfor<0, 5>([&](auto Aa) {
+              constexpr int a = LBM_CI(Aa);
+              Real acc = Real(0);
+              sfor<0, 5>([&](auto Bb) {
+                constexpr int b = LBM_CI(Bb);
+                if constexpr (has_ab<L>(a, b)) {
+                  constexpr double h = he(b, yv, c2);
+                  if constexpr (h != 0.0) acc = madd(Real(h), T[a][b], acc);
+                }
+              });
+              U[a] = acc;
+            });
+            sfor<0, count_yz<L>(yv, zv)>([&](auto J) {
+              constexpr int i = member_yz<L>(yv, zv, LBM_CI(J));
+              Real acc = Real(0);
+              sfor<0, 5>([&](auto Aa) {
+                constexpr int a = LBM_CI(Aa);
+                if constexpr (has_a<L>(a)) {
+                  constexpr double h = he(a, L::CX[i], c2) * (SHIFTED ? 1.0 : L::W[i]);
+                  if constexpr (h != 0.0) acc = madd(Real(h), U[a], acc);
+                }
+              });
+              emit(IC<i>{}, acc);
+            });
+          }
+        });
+      }
+    });
+  }
 }
 
 }  // namespace lbm

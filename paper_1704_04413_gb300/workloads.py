@@ -71,6 +71,52 @@ def shear_wave(nx: int, ny: int, amplitude: float, mode: int = 1) -> Fields:
     return Fields(np.ones((ny, nx)), ux, np.zeros((ny, nx)), None, grad)
 
 
+def taylor_green_3d_box(nx: int, ny: int, nz: int, u0: float):
+    """The Taylor-Green vortex of taylor_green_3d on an nx x ny x nz periodic box (wavenumber 2 pi / n per
+    axis); same layout of the returned arrays."""
+    kx, ky, kz = 2.0 * np.pi / nx, 2.0 * np.pi / ny, 2.0 * np.pi / nz
+    X = np.arange(nx, dtype=np.float64)[None, None, :] * kx
+    Y = np.arange(ny, dtype=np.float64)[None, :, None] * ky
+    Z = np.arange(nz, dtype=np.float64)[:, None, None] * kz
+    shape = (nz, ny, nx)
+    sx, cx, sy, cy, sz, cz = np.sin(X), np.cos(X), np.sin(Y), np.cos(Y), np.sin(Z), np.cos(Z)
+    u = np.zeros((3,) + shape)
+    u[0] = u0 * sx * cy * cz
+    u[1] = -u0 * cx * sy * cz
+    g = np.zeros((9,) + shape)
+    g[0] = u0 * kx * cx * cy * cz
+    g[1] = -u0 * ky * sx * sy * cz
+    g[2] = -u0 * kz * sx * cy * sz
+    g[3] = u0 * kx * sx * sy * cz
+    g[4] = -u0 * ky * cx * cy * cz
+    g[5] = u0 * kz * cx * sy * sz
+    return np.ones(shape), u, g
+
+
+def taylor_green_3d(n: int, u0: float):
+    """Three-dimensional Taylor-Green vortex on a periodic n^3 box, rho = 1:
+    u_x = u0 sin(kx) cos(ky) cos(kz), u_y = -u0 cos(kx) sin(ky) cos(kz), u_z = 0, k = 2 pi / n.
+    Returns rho [n][n][n], u [3][n][n][n] and grad [9][n][n][n] with component 3a + b = d u_a / d x_b
+    (arrays indexed [z][y][x])."""
+    k = 2.0 * np.pi / n
+    c = np.arange(n, dtype=np.float64) * k
+    sx, cx = np.sin(c)[None, None, :], np.cos(c)[None, None, :]
+    sy, cy = np.sin(c)[None, :, None], np.cos(c)[None, :, None]
+    sz, cz = np.sin(c)[:, None, None], np.cos(c)[:, None, None]
+    shape = (n, n, n)
+    u = np.zeros((3,) + shape)
+    u[0] = u0 * sx * cy * cz
+    u[1] = -u0 * cx * sy * cz
+    g = np.zeros((9,) + shape)
+    g[0] = u0 * k * cx * cy * cz
+    g[1] = -u0 * k * sx * sy * cz
+    g[2] = -u0 * k * sx * cy * sz
+    g[3] = u0 * k * sx * sy * cz
+    g[4] = -u0 * k * cx * cy * cz
+    g[5] = u0 * k * cx * sy * sz
+    return np.ones(shape), u, g
+
+
 def riemann_tube(nx: int, ny: int, left, right, x0: int | None = None) -> Fields:
     """Piecewise-constant states (rho, u, theta) left of x0 and right of it (x0 = nx/2 by default)."""
     x0 = nx // 2 if x0 is None else x0

@@ -133,10 +133,11 @@ def test_init_and_moments_match_oracle(name, storage):
     assert np.max(np.abs(r - r_ref)) <= tol * 10 and np.max(np.abs(v - u_ref)) <= tol * 10
 
 
+@pytest.mark.parametrize("nx", [140, 144])  # 140: rows not whole 16-byte units (direct loads); 144: staged
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
 @pytest.mark.parametrize("name", ["D3Q19", "D3Q27", "D3V39"])
-def test_shifted_16bit_storage(name, storage, tol):
-    nz, ny, nx = shape_for(name)
+def test_shifted_16bit_storage(name, storage, tol, nx):
+    nz, ny, _ = shape_for(name)
     f = random_state(name, (nz, ny, nx), 5)
     p = o.Params3(name, nx, ny, nz, 0.7, "rr", hermite_order=2)
     ref = o.step(p, f)
@@ -186,3 +187,40 @@ def test_shear_wave_decays_at_nu_k2(name):
         m.lbm3_moments(c.ctx, None, v)
     rate = math.log(a0 / np.abs(v[0]).max()) / n
     assert rate == pytest.approx(nu * k * k, rel=0.04)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (0, 1, 1)])
+@pytest.mark.parametrize("storage,nx", [("f64", 8), ("f64", 264), ("f32", 520)])
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27", "D3V39"])
+def test_staged_tiles_and_wraps(name, storage, nx, bc):
+    """Grids periodic in x with whole 16-byte rows take the staged kernel: a row that fits one tile (nx = 8)
+    is staged whole and wrapped by index; longer rows (FP64 264 = three 128-cell tiles, FP32 520 = three
+    256-cell tiles, the last ragged) get the wrapped columns as copies of their edge tiles; zero-gradient
+    y and z faces clamp the source rows of the staged copies.  Three steps."""
+    nz, ny = (9, 8) if o.lattice(name).xi.max() > 1 else (5, 6)
+    f = random_state(name, (nz, ny, nx), 13)
+    p = o.Params3(name, nx, ny, nz, 0.7, "rr", hermite_order=2, bc=bc)
+    ref = o.step(p, f, 3)
+    with Ctx3(name, nx, ny, nz, 0.7, "rr", 2, 0, storage, bc) as c:
+        c.set_oracle_f(f)
+        c.m.lbm3_step(c.ctx, 3)
+        got = c.get_oracle_f()
+    if storage == "f64":
+        assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-12
+    else:
+        assert pop_rel(got, ref, o.lattice(name).w) <= 3 * TOL["f32"]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_staged_ring_reuse(storage):
+    """Enough row tiles (2 x 64 x 48 = 6144) that every persistent block walks several rounds of its stage ring,
+    so each stage's barrier completes phases of both parities."""
+    name, nz, ny, nx = "D3Q19", 48, 64, 256
+    f = random_state(name, (nz, ny, nx), 17)
+    p = o.Params3(name, nx, ny, nz, 0.62, "rr", hermite_order=2)
+    ref = o.step(p, f, 2)
+    with Ctx3(name, nx, ny, nz, 0.62, "rr", 2, 0, storage) as c:
+        c.set_oracle_f(f)
+        c.m.lbm3_step(c.ctx, 2)
+        got = c.get_oracle_f()
+    assert pop_rel(got, ref, o.lattice(name).w) <= 2 * TOL[storage]
