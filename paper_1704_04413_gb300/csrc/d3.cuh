@@ -26,9 +26,19 @@ struct PullOffsets3 {
   int cy[Q], cz[Q];  // velocity components, indexed at run time by the copy-issuing lanes
 };
 
-template <class L>
+// Blocks per SM the register allocation must allow.  D3Q103 in FP32 fits 128 registers without spills
+// (four 128-thread blocks a SM, against two at the 255 it takes unbounded); in FP64 a cap spills kilobytes.
+template <class L, class Real>
 struct Step3Blocks {
-  static constexpr int MIN = L::Q > 40 ? 1 : (L::Q > 20 ? 3 : 4);
+  static constexpr int MIN = L::Q > 40 ? (sizeof(Real) == 4 ? 4 : 1) : (L::Q > 20 ? 3 : 4);
+};
+
+// The same for the staged kernel's 160-thread blocks.  Measured at 256^3: D3Q27 and D3V39 with 16-bit
+// storage gain from a fourth block (96 registers, 1.07x); their FP32 kernels (three blocks fit the
+// shared memory anyway) and D3Q19 (at 72 registers for five blocks) lose to the tighter schedule.
+template <class L, class S>
+struct Staged3Blocks {
+  static constexpr int MIN = L::Q > 20 ? (sizeof(S) == 2 ? 4 : 3) : 4;
 };
 
 // Storage formats built per lattice: all five, except D3Q103 (FP64 and FP32 only: its kernels are large
@@ -42,7 +52,7 @@ struct Storages3 {
 // the y and z edges (block-uniform) take one load sequence with the x wrap folded into a base pointer per
 // x-velocity; the other rows (and grids narrower than the stencil) the general path.
 template <class L, int COLL, class Real, class S>
-__global__ void __launch_bounds__(STEP_BX, Step3Blocks<L>::MIN)
+__global__ void __launch_bounds__(STEP_BX, Step3Blocks<L, Real>::MIN)
     k_step3(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, CollParams<Real> P,
             const __grid_constant__ PullOffsets3<L::Q> off) {
   const int row = blockIdx.x / nbx;
@@ -156,7 +166,7 @@ struct TileWalk {
 };
 
 template <class L, int COLL, class Real, class S>
-__global__ void __launch_bounds__(Stage3<L, S>::THREADS, Step3Blocks<L>::MIN)
+__global__ void __launch_bounds__(Stage3<L, S>::THREADS, Staged3Blocks<L, S>::MIN)
     k_step3_staged(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, long long ntiles,
                    CollParams<Real> P, const __grid_constant__ PullOffsets3<L::Q> off) {
   using St = Stage3<L, S>;
