@@ -207,6 +207,9 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
 #ifndef LBM_STEP2_MINB_LARGE
 #define LBM_STEP2_MINB_LARGE 2
 #endif
+#ifndef LBM_STEP2_MINB_LARGE_F16
+#define LBM_STEP2_MINB_LARGE_F16 5
+#endif
 #ifndef LBM_STEP_PAIRS_LARGE_16
 #define LBM_STEP_PAIRS_LARGE_16 1
 #endif
@@ -264,9 +267,13 @@ __device__ __forceinline__ void st_pair<__nv_bfloat16>(__nv_bfloat16* p, F2 v) {
   *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.v.x, v.v.y);
 }
 
-template <class L>
+// Blocks per SM of the pair kernel.  D2V37 with binary16 storage runs at 96 registers (five blocks, 24-28 B
+// of spills; 31.7 -> 35.3 GLUPS at 4096^2): its conversions gain from the extra warps, while the bfloat16
+// kernel (36.5 -> 35.0) and the others keep their unbounded allocation.
+template <class L, class S>
 struct Step2Blocks {
-  static constexpr int MIN = L::Q > 20 ? LBM_STEP2_MINB_LARGE : 1;
+  static constexpr int MIN =
+      L::Q > 20 ? (std::is_same<S, __half>::value ? LBM_STEP2_MINB_LARGE_F16 : LBM_STEP2_MINB_LARGE) : 1;
 };
 
 // Offsets of the pulled source / the store of population i as template accessors: from the kernel
@@ -365,7 +372,7 @@ __device__ __forceinline__ void step2_cells(const S* __restrict__ fin, S* __rest
 }
 
 template <class L, int COLL, class S>
-__global__ void __launch_bounds__(STEP_BX, Step2Blocks<L>::MIN)
+__global__ void __launch_bounds__(STEP_BX, Step2Blocks<L, S>::MIN)
     k_step2(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<F2> P,
             const __grid_constant__ PullOffsets<L::Q> off) {
   const int y = blockIdx.x / nbx;
