@@ -113,18 +113,6 @@ __global__ void __launch_bounds__(STEP_BX, Step3Blocks<L, Real>::MIN)
 // full barrier (the copied bytes) and an empty barrier (one arrival per compute warp), so the copies run up
 // to STAGES tiles ahead of the compute and no warp waits for another one's arithmetic.  The copy count, not
 // the byte count, is what the copy engine's throughput is spent on, hence the wide tiles.
-template <class S>
-__device__ __forceinline__ float sm_decode(S v);
-template <>
-__device__ __forceinline__ float sm_decode<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float sm_decode<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float sm_decode<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <>
-__device__ __forceinline__ float sm_decode<short>(short v) { return (float)v * (1.0f / kFix16); }
-__device__ __forceinline__ double sm_decode_d(double v) { return v; }
-
 template <class L, class S>
 struct Stage3 {
   static constexpr int UNIT = 16 / (int)sizeof(S);                           // cells per 16 bytes

@@ -11,7 +11,9 @@
 
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "collide.cuh"
+#include "lbm.h"
 
 namespace lbm {
 
@@ -80,6 +82,7 @@ template <int Q>
 struct PullOffsets {
   long long src[Q];
   long long dst[Q];
+  int cy[Q];  // y-velocity components, indexed at run time by the staged kernel's copy-issuing lanes
 };
 
 // Raw loads issued in program order (volatile asm keeps them ahead of the arithmetic that consumes
@@ -206,6 +209,9 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
 #endif
 #ifndef LBM_STEP2_MINB_LARGE
 #define LBM_STEP2_MINB_LARGE 2
+#endif
+#ifndef LBM_STEP_STAGED
+#define LBM_STEP_STAGED 1
 #endif
 #ifndef LBM_STEP2_MINB_LARGE_F16
 #define LBM_STEP2_MINB_LARGE_F16 5
@@ -383,13 +389,257 @@ __global__ void __launch_bounds__(STEP_BX, Step2Blocks<L, S>::MIN)
   step2_cells<L, COLL, S>(fin, fout, g, P, ParamOffsets<L::Q>{off}, x, y, xw);
 }
 
+
+// ---------------------------------------------------------------------------
+// Staged pair kernel for x-periodic grids whose rows are whole 16-byte units (the same collision as
+// k_step2).  A persistent block walks a contiguous run of row tiles of BXT = 512 cells.  Its producer warp
+// copies each population's pulled source row segment (row y - c_y) with one cp.async.bulk into a ring of
+// shared-memory stages (full barrier: the copied bytes; empty barrier: one arrival per compute warp); a row
+// that fits a tile is copied whole and wrapped by index, longer rows carry PAD cells of margin and their
+// edge tiles copy the wrapped columns.  4 compute warps take two cell pairs a thread per tile.  The copies
+// run ahead of the compute, so the bytes in flight no longer depend on the warps the registers allow.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ float sm_decode(S v);
+template <>
+__device__ __forceinline__ float sm_decode<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float sm_decode<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float sm_decode<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float sm_decode<short>(short v) { return (float)v * (1.0f / kFix16); }
+__device__ __forceinline__ double sm_decode_d(double v) { return v; }
+
+// Two neighbouring staged cells (p even: one aligned vector read).
+template <class S>
+__device__ __forceinline__ F2 sm_pair(const S* p);
+template <>
+__device__ __forceinline__ F2 sm_pair<float>(const float* p) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  return F2(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ F2 sm_pair<__half>(const __half* p) {
+  const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+  return F2(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ F2 sm_pair<__nv_bfloat16>(const __nv_bfloat16* p) {
+  const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  return F2(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ F2 sm_pair<short>(const short* p) {
+  const short2 v = *reinterpret_cast<const short2*>(p);
+  return F2((float)v.x * (1.0f / kFix16), (float)v.y * (1.0f / kFix16));
+}
+
+template <class L, class S>
+struct Stage2 {
+  static constexpr int UNIT = 16 / (int)sizeof(S);                           // cells per 16 bytes
+  static constexpr int PAD = (L::VMAX + UNIT - 1) / UNIT * UNIT;              // stencil margin, whole units
+  static constexpr int BXT = 512;                                             // cells per tile
+  static constexpr int W = BXT + 2 * PAD;                                     // cells per staged row
+  static constexpr int ROW_BYTES = W * (int)sizeof(S);
+  static constexpr int STAGE_BYTES = L::Q * ROW_BYTES;
+  static constexpr int STAGES_FIT = 64 * 1024 / STAGE_BYTES;
+  static constexpr int STAGES = STAGES_FIT < 2 ? 2 : (STAGES_FIT > 4 ? 4 : STAGES_FIT);
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 128;
+  static constexpr int CW = 4;                                                // compute warps
+  static constexpr int THREADS = 32 * CW + 32;                                // + the producer warp
+  static constexpr int PAIRS = BXT / (2 * 32 * CW);                           // cell pairs a thread per tile
+  // 16-bit storage of D2Q9 and D2V17 (measured at 4096^2: D2Q9 FP16 121 -> 131, D2V17 80.8 -> 83.5
+  // GLUPS); FP32 stays on k_step2, which already reaches the HBM roofline there (staged: 95 -> 78), and
+  // D2V37 takes 226-250 registers here (one block a SM)
+  static constexpr bool ENABLED = L::Q <= 20 && sizeof(S) == 2;
+  static constexpr int MIN_BLOCKS = L::Q <= 9 ? 5 : 4;
+};
+
+template <class L, int COLL, class S>
+__global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCKS)
+    k_step2_staged(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbt, long long ntiles,
+                   CollParams<F2> P, const __grid_constant__ PullOffsets<L::Q> off, int* status) {
+  using St = Stage2<L, S>;
+  constexpr int NS = St::STAGES;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full[NS], empty[NS];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], St::CW);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool whole_rows = nbt == 1;
+  const long long t_begin = blockIdx.x * ntiles / gridDim.x;
+  const int n_mine = (int)((blockIdx.x + 1LL) * ntiles / gridDim.x - t_begin);
+  const int y_begin = (int)(t_begin / nbt), bx_begin = (int)(t_begin - (long long)y_begin * nbt);
+
+  if (warp == St::CW) {
+    // producer: tile k of this block goes to stage k % NS once the compute warps released its previous use
+    int k = 0, bx = bx_begin, y = y_begin;
+    bool ok = true;
+    for (; k < n_mine; ++k) {
+      const int s = k % NS;
+      if (k >= NS) ok = mbar_wait(&empty[s], (uint32_t)(((k / NS) + 1) & 1));
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const int x0 = bx * St::BXT;
+      const int xa = max(x0 - St::PAD, 0), xb = min(x0 + St::BXT + St::PAD, g.nx);
+      const int left = (!whole_rows && x0 - St::PAD < 0) ? St::PAD : 0;
+      const int right =
+          (!whole_rows && x0 + St::BXT + St::PAD > g.nx) ? min(x0 + St::BXT + St::PAD - g.nx, St::PAD) : 0;
+      const uint32_t per_row = (uint32_t)(xb - xa + left + right) * (uint32_t)sizeof(S);
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], per_row * (uint32_t)L::Q);
+      __syncwarp();
+      unsigned char* st = sm + (size_t)s * St::STAGE_BYTES;
+      const char* base = reinterpret_cast<const char*>(fin);
+      for (int i = lane; i < L::Q; i += 32) {  // one population per lane
+        const int ys = src_coord(y, off.cy[i], g.ny, g.bcy);
+        const char* src = base + off.dst[i] + (long long)ys * g.pitch * (long long)sizeof(S);
+        unsigned char* dst = st + i * St::ROW_BYTES;
+        bulk_g2s(dst + (xa - x0 + St::PAD) * (int)sizeof(S), src + (long long)xa * sizeof(S),
+                 (uint32_t)(xb - xa) * (uint32_t)sizeof(S), &full[s]);
+        if (left)
+          bulk_g2s(dst, src + (long long)(g.nx - St::PAD) * sizeof(S), (uint32_t)St::PAD * (uint32_t)sizeof(S),
+                   &full[s]);
+        if (right)
+          bulk_g2s(dst + (g.nx - x0 + St::PAD) * (int)sizeof(S), src, (uint32_t)right * (uint32_t)sizeof(S),
+                   &full[s]);
+      }
+      if (++bx == nbt) {
+        bx = 0;
+        ++y;
+      }
+    }
+    if (!ok && lane == 0) {
+      // a compute warp stopped releasing stages: flag it, and wait (bounded) for the copies that may still
+      // be in flight, the last use of every stage, before the block's shared memory is released
+      atomicExch(status, LBM_ETIMEOUT);
+      for (int j = 1; j <= NS; ++j)
+        if (k - j >= 0) mbar_wait(&full[(k - j) % NS], (uint32_t)(((k - j) / NS) & 1));
+    }
+    return;
+  }
+
+  // compute warps
+  int bx = bx_begin, y = y_begin;
+  for (int k = 0; k < n_mine; ++k) {
+    const int s = k % NS;
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((k / NS) & 1)))) {
+      if (lane == 0) atomicExch(status, LBM_ETIMEOUT);
+      return;
+    }
+    const int x0 = bx * St::BXT;
+    const S* sp = reinterpret_cast<const S*>(sm + (size_t)s * St::STAGE_BYTES);
+    sfor<0, St::PAIRS>([&](auto Pp) {
+      constexpr int pr = LBM_CI(Pp);
+      const int x = x0 + pr * (64 * St::CW) + 2 * tid;
+      const bool active = x < g.nx;
+      const bool two = x + 1 < g.nx;
+      F2 q[L::Q];
+      if (active) {
+        // staged positions of the pulled sources x - cx and x + 1 - cx, per x-velocity; an even cx moves
+        // both cells of the pair together (x is even), so it is one aligned vector read
+        int pos0[2 * L::VMAX + 1], pos1[2 * L::VMAX + 1];
+        sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+          constexpr int j = LBM_CI(J);
+          int xs0 = x - (j - L::VMAX), xs1 = x + 1 - (j - L::VMAX);
+          if (whole_rows) {
+            xs0 += (xs0 < 0 ? g.nx : 0) - (xs0 >= g.nx ? g.nx : 0);
+            xs1 += (xs1 < 0 ? g.nx : 0) - (xs1 >= g.nx ? g.nx : 0);
+          }
+          pos0[j] = xs0 - x0 + St::PAD;
+          pos1[j] = xs1 - x0 + St::PAD;
+        });
+        sfor<0, L::Q>([&](auto I) {
+          constexpr int i = LBM_CI(I);
+          constexpr int j = L::CX[i] + L::VMAX;
+          const S* row = sp + i * St::W;
+          if constexpr (L::CX[i] % 2 == 0) {
+            q[i] = sm_pair<S>(row + pos0[j]);
+          } else {
+            q[i] = F2(sm_decode<S>(row[pos0[j]]), sm_decode<S>(row[pos1[j]]));
+          }
+        });
+      }
+      if constexpr (pr == St::PAIRS - 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp has read the stage: the producer may refill it
+      }
+      if (active) {
+        collide<L, COLL, false, Store<S>::SHIFTED>(q, P);
+        char* o = reinterpret_cast<char*>(fout + ((long long)y * g.pitch + x));
+        if (two) {
+          sfor<0, L::Q>([&](auto I) {
+            constexpr int i = LBM_CI(I);
+            st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), q[i]);
+          });
+        } else {
+          sfor<0, L::Q>([&](auto I) {
+            constexpr int i = LBM_CI(I);
+            Store<S>::st(reinterpret_cast<S*>(o + off.dst[i]), q[i].v.x);
+          });
+        }
+      }
+    });
+    if (++bx == nbt) {
+      bx = 0;
+      ++y;
+    }
+  }
+}
+
+// Blocks of the staged pair kernel resident per SM, times the SM count (per device, taken once).
+template <class L, int COLL, class S>
+inline int staged2_grid(int* out) {
+  static int dev_cached = -1, grid_cached = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  if (dev != dev_cached) {
+    auto k = k_step2_staged<L, COLL, S>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage2<L, S>::SMEM);
+    if (e != cudaSuccess) return (int)e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Stage2<L, S>::THREADS, Stage2<L, S>::SMEM);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return (int)e;
+    if (per_sm < 1) return (int)cudaErrorInvalidConfiguration;
+    grid_cached = per_sm * sms;
+    dev_cached = dev;
+  }
+  *out = grid_cached;
+  return 0;
+}
+
 template <class L, int COLL, class S>
 inline cudaError_t launch_step2_t(const void* fin, void* fout, const StepGeom& g, const CollParamsD& pd,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int* err = nullptr) {
   PullOffsets<L::Q> off;
   for (int i = 0; i < L::Q; ++i) {
     off.dst[i] = (long long)i * g.plane * (long long)sizeof(S);
     off.src[i] = off.dst[i] - ((long long)L::CY[i] * g.pitch + L::CX[i]) * (long long)sizeof(S);
+    off.cy[i] = L::CY[i];
+  }
+  using St = Stage2<L, S>;
+  if constexpr (St::ENABLED) {
+    if (LBM_STEP_STAGED && err != nullptr && g.bcx == BC_PERIODIC && g.nx % St::UNIT == 0 && g.nx >= St::PAD) {
+    const int nbt = (g.nx + St::BXT - 1) / St::BXT;
+    const long long ntiles = (long long)nbt * g.ny;
+    int grid = 0;
+    const int e = staged2_grid<L, COLL, S>(&grid);
+    if (e) return (cudaError_t)e;
+    const long long nb = ntiles < grid ? ntiles : grid;
+    k_step2_staged<L, COLL, S><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
+        (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, err);
+    return cudaGetLastError();
+    }
   }
   const int nbx = (g.nx + 2 * STEP_BX - 1) / (2 * STEP_BX);
   const long long nblocks = (long long)nbx * g.ny;
@@ -475,7 +725,7 @@ inline cudaError_t launch_step_fd(int prec, const void* fin, void* fout, const S
 
 template <class L, int COLL, bool THERMAL>
 inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const StepGeom& g,
-                                    const CollParamsD& pd, cudaStream_t st) {
+                                    const CollParamsD& pd, cudaStream_t st, int* err) {
   // Two cells per thread pay off while the pair's registers stay low (D2Q9, D2V17).  D2V37 keeps one
   // cell per thread in FP32 and FP64 (HBM-bound: its 20 resident warps per SM keep more bytes in flight
   // than the pair kernel's 16), but with 16-bit storage, which is issue-bound, the packed FP32x2
@@ -484,19 +734,19 @@ inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const
   // the scalar kernel's shorter blocks are as fast or faster.
   if constexpr (!THERMAL && LBM_STEP_PAIRS_LARGE_16 && L::Q > 20) {
     if ((long long)g.nx * g.ny >= LBM_STEP_PAIRS_LARGE_16_MIN) switch (prec) {
-      case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st);
-      case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st);
-      case PREC_I16: return launch_step2_t<L, COLL, short>(fin, fout, g, pd, st);
+      case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st, err);
+      case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st, err);
+      case PREC_I16: return launch_step2_t<L, COLL, short>(fin, fout, g, pd, st, err);
       default: break;
     }
   }
   if constexpr (!THERMAL && LBM_STEP_PAIRS && L::Q <= 20) {
     switch (prec) {
       case PREC_F64: return launch_step_t<L, COLL, THERMAL, double, double>(fin, fout, g, pd, st);
-      case PREC_F32: return launch_step2_t<L, COLL, float>(fin, fout, g, pd, st);
-      case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st);
-      case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st);
-      case PREC_I16: return launch_step2_t<L, COLL, short>(fin, fout, g, pd, st);
+      case PREC_F32: return launch_step2_t<L, COLL, float>(fin, fout, g, pd, st, err);
+      case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st, err);
+      case PREC_BF16: return launch_step2_t<L, COLL, __nv_bfloat16>(fin, fout, g, pd, st, err);
+      case PREC_I16: return launch_step2_t<L, COLL, short>(fin, fout, g, pd, st, err);
     }
   } else {
     switch (prec) {
@@ -513,13 +763,13 @@ inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const
 // fd_mom: moments buffer of the finite-difference variant (RR only), nullptr = a1 by projection.
 template <class L, bool THERMAL>
 inline cudaError_t launch_step_lattice(int coll, int prec, const void* fin, void* fout, const StepGeom& g,
-                                       const CollParamsD& pd, void* fd_mom, cudaStream_t st) {
+                                       const CollParamsD& pd, void* fd_mom, cudaStream_t st, int* err) {
   if (fd_mom) return coll == COLL_RR ? launch_step_fd<L, THERMAL>(prec, fin, fout, g, pd, fd_mom, st)
                                      : cudaErrorInvalidValue;
   switch (coll) {
-    case COLL_BGK: return launch_step_prec<L, COLL_BGK, THERMAL>(prec, fin, fout, g, pd, st);
-    case COLL_PR: return launch_step_prec<L, COLL_PR, THERMAL>(prec, fin, fout, g, pd, st);
-    case COLL_RR: return launch_step_prec<L, COLL_RR, THERMAL>(prec, fin, fout, g, pd, st);
+    case COLL_BGK: return launch_step_prec<L, COLL_BGK, THERMAL>(prec, fin, fout, g, pd, st, err);
+    case COLL_PR: return launch_step_prec<L, COLL_PR, THERMAL>(prec, fin, fout, g, pd, st, err);
+    case COLL_RR: return launch_step_prec<L, COLL_RR, THERMAL>(prec, fin, fout, g, pd, st, err);
   }
   return cudaErrorInvalidValue;
 }

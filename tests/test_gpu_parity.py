@@ -330,3 +330,28 @@ def test_large_grid_16bit_d2v37_sampled_parity(storage, tol):
     w = Lt.w[:, None]
     dev = np.abs(ref / w - 1.0).max()
     assert np.max(np.abs(got - ref) / w) <= tol * dev
+
+
+@pytest.mark.parametrize("bcy", [0, 1])
+@pytest.mark.parametrize("nx", [64, 1040])
+@pytest.mark.parametrize("storage,tol", [("f32", None), ("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
+@pytest.mark.parametrize("name", ["D2Q9", "D2V17"])
+def test_staged_pair_tiles(name, storage, tol, nx, bcy):
+    """With 16-bit storage, x-periodic grids with whole 16-byte rows take the staged pair kernel: nx = 64 is
+    one tile (the row staged whole, wrapped by index), nx = 1040 two 512-cell tiles and a ragged one whose
+    edge tiles copy the wrapped columns; a zero-gradient y edge clamps the staged source rows.  FP32 runs the
+    same cases through the direct pair kernel.  Three RR steps."""
+    ny, tau, steps = 6, 0.62, 3
+    Lt = orc.lattice(name)
+    f = oracle_state(name, nx, ny, 21, False, neq=Lt.nmax)
+    op = orc.params(name, nx, ny, tau, "rr", Lt.nmax, bc_x=0, bc_y=bcy)
+    ref = orc.step(op, f, steps)
+    with Ctx(name, nx, ny, tau, "rr", Lt.nmax, 0, storage, False, bcx=0, bcy=bcy) as c:
+        c.set_oracle_f(f)
+        c.step(steps)
+        got = c.get_oracle_f()
+    if storage == "f32":
+        assert pop_rel(got, ref, Lt.w) <= steps * TOL_COLL["f32"]
+    else:
+        w = Lt.w[:, None, None]
+        assert np.max(np.abs(got - ref) / w) <= steps * tol * np.abs(f / w - 1.0).max()
