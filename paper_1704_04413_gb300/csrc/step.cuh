@@ -73,6 +73,9 @@ __device__ __forceinline__ int src_coord(int x, int c, int n, int bc) {
 #ifndef LBM_STEP_MINB_LARGE
 #define LBM_STEP_MINB_LARGE 5
 #endif
+#ifndef LBM_STEP_MINB_LARGE_ISO32
+#define LBM_STEP_MINB_LARGE_ISO32 7
+#endif
 constexpr int STEP_BX = LBM_STEP_BX;  // cells (threads) per block
 
 // Byte offsets of the pulled source of population i relative to the cell's address in plane 0,
@@ -120,10 +123,14 @@ __device__ __forceinline__ auto ld_raw<short>(const char* p) {
   return (float)u * (1.0f / kFix16);
 }
 
-// Registers: the D2V37 kernels are capped so that at least LBM_STEP_MINB_LARGE blocks fit on an SM.
-template <class L>
+// Registers: the D2V37 kernels are capped so that at least LBM_STEP_MINB_LARGE blocks fit on an SM; the
+// isothermal ones with FP32 arithmetic fit 72 registers without spills, seven blocks (28 warps) a SM:
+// measured on the 1024^2 shear layer, 18.3 -> 18.9 GLUPS alone and 0.748 -> 0.776 of the measured copy
+// in the benchmark; FP64 and thermal kernels would spill at that cap.
+template <class L, bool THERMAL, class Real>
 struct StepBlocks {
-  static constexpr int MIN = L::Q > 20 ? LBM_STEP_MINB_LARGE : 1;
+  static constexpr int MIN =
+      L::Q > 20 ? ((!THERMAL && sizeof(Real) == 4) ? LBM_STEP_MINB_LARGE_ISO32 : LBM_STEP_MINB_LARGE) : 1;
 };
 
 // One block = STEP_BX consecutive cells of one row; the grid is 1D over (row, column block).
@@ -131,7 +138,7 @@ struct StepBlocks {
 // the pass k_stream_moments writes it); neighbours follow the streaming rule (periodic wrap, or the
 // clamped edge cell on a zero-gradient axis).
 template <class L, int COLL, bool THERMAL, class Real, class S, bool FD = false>
-__global__ void __launch_bounds__(STEP_BX, StepBlocks<L>::MIN)
+__global__ void __launch_bounds__(STEP_BX, StepBlocks<L, THERMAL, Real>::MIN)
     k_step(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbx, CollParams<Real> P,
            const __grid_constant__ PullOffsets<L::Q> off, const Real* __restrict__ mom = nullptr) {
   const int y = blockIdx.x / nbx;
