@@ -456,10 +456,12 @@ struct Stage2 {
   static constexpr int CW = 4;                                                // compute warps
   static constexpr int THREADS = 32 * CW + 32;                                // + the producer warp
   static constexpr int PAIRS = BXT / (2 * 32 * CW);                           // cell pairs a thread per tile
-  // 16-bit storage of D2Q9 and D2V17 (measured at 4096^2: D2Q9 FP16 121 -> 131, D2V17 80.8 -> 83.5
-  // GLUPS); FP32 stays on k_step2, which already reaches the HBM roofline there (staged: 95 -> 78), and
-  // D2V37 takes 226-250 registers here (one block a SM)
-  static constexpr bool ENABLED = L::Q <= 20 && sizeof(S) == 2;
+  // binary16 and bfloat16 storage of D2Q9 and D2V17 (measured at 4096^2: D2Q9 FP16 121 -> 131, D2V17
+  // 80.8 -> 83.5 GLUPS); FP32 stays on k_step2, which already reaches the HBM roofline there (staged: 95
+  // -> 78), as does the fixed-point format (staged: D2Q9 119.7 -> 110.4), and D2V37 takes 226-250
+  // registers here (one block a SM)
+  static constexpr bool ENABLED =
+      L::Q <= 20 && (std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value);
   static constexpr int MIN_BLOCKS = L::Q <= 9 ? 5 : 4;
 };
 

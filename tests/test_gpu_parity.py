@@ -337,10 +337,10 @@ def test_large_grid_16bit_d2v37_sampled_parity(storage, tol):
 @pytest.mark.parametrize("storage,tol", [("f32", None), ("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
 @pytest.mark.parametrize("name", ["D2Q9", "D2V17"])
 def test_staged_pair_tiles(name, storage, tol, nx, bcy):
-    """With 16-bit storage, x-periodic grids with whole 16-byte rows take the staged pair kernel: nx = 64 is
-    one tile (the row staged whole, wrapped by index), nx = 1040 two 512-cell tiles and a ragged one whose
-    edge tiles copy the wrapped columns; a zero-gradient y edge clamps the staged source rows.  FP32 runs the
-    same cases through the direct pair kernel.  Three RR steps."""
+    """With binary16 or bfloat16 storage, x-periodic grids with whole 16-byte rows take the staged pair
+    kernel: nx = 64 is one tile (the row staged whole, wrapped by index), nx = 1040 two 512-cell tiles and a
+    ragged one whose edge tiles copy the wrapped columns; a zero-gradient y edge clamps the staged source
+    rows.  FP32 and fixed point run the same cases through the direct pair kernel.  Three RR steps."""
     ny, tau, steps = 6, 0.62, 3
     Lt = orc.lattice(name)
     f = oracle_state(name, nx, ny, 21, False, neq=Lt.nmax)
