@@ -34,23 +34,24 @@ __global__ void k_init(const double* __restrict__ rho, const double* __restrict_
   const long long n = (long long)g.nx * g.ny;
   if (c >= n) return;
   const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+  // FP64 arithmetic for FP64 storage, FP32 otherwise (the state is stored in 32 bits or fewer)
+  using Real = typename std::conditional<std::is_same<S, double>::value, double, float>::type;
   constexpr double c2 = L::CS2;
-  const double r = rho[c], u = ux[c], v = uy[c];
-  const double th = (THERMAL && theta) ? theta[c] : 1.0;
-  const double e = c2 * (th - 1.0);
-  double A[5][5], B[5][5] = {}, C[5][5];
+  const Real r = (Real)rho[c], u = (Real)ux[c], v = (Real)uy[c];
+  const Real th = (THERMAL && theta) ? (Real)theta[c] : Real(1);
+  const Real e = Real(c2) * (th - Real(1));
+  Real A[5][5], B[5][5] = {}, C[5][5];
   equilibrium_coefficients<L, THERMAL>(r, u, v, e, A);
   const bool neq_part = grad != nullptr;
   if (neq_part) {
     // d[a][b] = d_b u_a
-    const double d[2][2] = {{grad[c], grad[n + c]}, {grad[2 * n + c], grad[3 * n + c]}};
-    const double div = d[0][0] + d[1][1];
-    const double pre = -ip.tau * r * c2 * th;
-    double sxx = 2.0 * d[0][0], syy = 2.0 * d[1][1];
+    const Real d[2][2] = {{(Real)grad[c], (Real)grad[n + c]}, {(Real)grad[2 * n + c], (Real)grad[3 * n + c]}};
+    const Real div = d[0][0] + d[1][1];
+    const Real pre = -(Real)ip.tau * r * Real(c2) * th;
+    Real sxx = Real(2) * d[0][0], syy = Real(2) * d[1][1];
     if (THERMAL) {  // traceless part, D = 2
-      constexpr double D = 2.0;
-      sxx -= (2.0 / D) * div;
-      syy -= (2.0 / D) * div;
+      sxx -= div;
+      syy -= div;
     }
     B[2][0] = pre * sxx;
     B[0][2] = pre * syy;
@@ -65,16 +66,16 @@ __global__ void k_init(const double* __restrict__ rho, const double* __restrict_
       constexpr int b = nn - a;
       if constexpr (L::keep(a, b)) {
         constexpr double sc = 1.0 / (factorial(a) * factorial(b) * ipow(c2, a + b));
-        double val = (nn <= ip.neq) ? A[a][b] : 0.0;
+        Real val = (nn <= ip.neq) ? A[a][b] : Real(0);
         if constexpr (nn >= 2) val += B[a][b];
-        if constexpr (Store<S>::SHIFTED) val *= ip.s;
-        C[a][b] = val * sc;
+        if constexpr (Store<S>::SHIFTED) val *= (Real)ip.s;
+        C[a][b] = val * Real(sc);
       }
     });
   });
   const long long o = (long long)y * g.pitch + x;
-  const double shift = Store<S>::SHIFTED ? -ip.s * ip.rho0 : 0.0;
-  rebuild<L, Store<S>::SHIFTED>(C, [&](auto I, double acc) {
+  const Real shift = Store<S>::SHIFTED ? (Real)(-ip.s * ip.rho0) : Real(0);
+  rebuild<L, Store<S>::SHIFTED>(C, [&](auto I, Real acc) {
     constexpr int i = LBM_CI(I);
     Store<S>::st(f + (long long)i * g.plane + o, acc + shift);
   });
