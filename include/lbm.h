@@ -230,7 +230,8 @@ int lbm_batch_autotune(lbm_batch *b, int steps, double *best_ms);
 
 /* ------------------------------------------------------------------------
  * Learned closure for coarse grids (a per-cell MLP, not part of the paper's
- * method: its fallback and the judge of its error is the plain RR step).
+ * method; the plain RR step is both what it falls back to and the reference its
+ * error is measured against).
  * Features of a cell: (rho - 1, ux, uy) / u0 of its 3x3 neighbourhood
  * (periodic), 27 values padded to LBM_CLOSURE_IN, BF16 row-major.  Outputs:
  * LBM_CLOSURE_OUT FP32 per cell, the first 3 being the subgrid stress

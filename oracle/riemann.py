@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (part of the oracle).  Textbook Godunov exact solver
 (pressure function with shock / rarefaction branches, Newton iteration for the
-star pressure, self-similar sampling); used to judge the Sod shock tubes of
-Sec. III.C, where the single-population D2V37 model has gamma = (D+2)/D = 2.
+star pressure, self-similar sampling); the exact solution the Sod shock tubes of
+Sec. III.C are checked against, where the single-population D2V37 model has
+gamma = (D+2)/D = 2.
 """
 from __future__ import annotations
 
