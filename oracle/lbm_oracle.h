@@ -63,7 +63,7 @@ typedef struct {
                          GenRegCollision with one time per order, Sec. II.B); 0 = tau.  PR/RR only */
   int a1_source;      /* RR only: 0 = a1^(2) (and the thermal a1^(3)) by projection of f - f^(0) (Eq. a12Proj,
                          Eq. TempGradLBM); 1 = by finite differences of the velocity (and temperature)
-                         field (Sec. II.E: "or using finite differences") */
+                         field (Sec. II.E allows finite differences in place of the projection) */
 } orc_params;
 
 /* Gradients handed to the finite-difference collision, per cell:

@@ -229,7 +229,7 @@ __host__ __device__ constexpr double kappa(int a, int b) {
 // With CLOSURE, da[0..2] is added to the projected a1^(2) (xx, xy, yy) before the recursion (the
 // learned coarse-grid closure; closure.cu).  With FD (RR only), a1^(2) and the thermal temperature-gradient
 // terms come from the gradients grad[0..5] = d ux/dx, d ux/dy, d uy/dx, d uy/dy, d theta/dx, d theta/dy
-// (Sec. II.E: "or using finite differences"):
+// (Sec. II.E allows finite differences in place of the projection):
 //   a1^(2)_ab = -tau rho cs^2 theta (d_a u_b + d_b u_a - delta_ab div u) (thermal, D = 2), -tau rho cs^2 S
 //   (isothermal); mu cs^2 d_g theta = tau_3 rho cs^4 theta d_g theta in place of Eq. TempGradLBM.
 template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real, bool CLOSURE = false, bool FD = false>
