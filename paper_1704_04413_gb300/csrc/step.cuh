@@ -736,11 +736,11 @@ template <class L, int COLL, bool THERMAL>
 inline cudaError_t launch_step_prec(int prec, const void* fin, void* fout, const StepGeom& g,
                                     const CollParamsD& pd, cudaStream_t st, int* err) {
   // Two cells per thread pay off while the pair's registers stay low (D2Q9, D2V17).  D2V37 keeps one
-  // cell per thread in FP32 and FP64 (HBM-bound: its 20 resident warps per SM keep more bytes in flight
-  // than the pair kernel's 16), but with 16-bit storage, which is issue-bound, the packed FP32x2
-  // arithmetic wins from LBM_STEP_PAIRS_LARGE_16_MIN cells up (measured on GB300 at 4096^2: BF16 27.4
-  // -> 36.6 GLUPS, FP16 27.4 -> 31.7, fixed point 26.1 -> 30.7); below that the grid is a few waves and
-  // the scalar kernel's shorter blocks are as fast or faster.
+  // cell per thread in FP32 and FP64 (HBM-bound: its 28 resident warps per SM in FP32, 20 in FP64, keep
+  // more bytes in flight than the pair kernel's 16-20), but with 16-bit storage, which is issue-bound, the
+  // packed FP32x2 arithmetic wins from LBM_STEP_PAIRS_LARGE_16_MIN cells up (measured on GB300 at 4096^2:
+  // BF16 27.4 -> 36.6 GLUPS, FP16 27.4 -> 35.4, fixed point 26.1 -> 30.7); below that the grid is a few
+  // waves and the scalar kernel's shorter blocks are as fast or faster.
   if constexpr (!THERMAL && LBM_STEP_PAIRS_LARGE_16 && L::Q > 20) {
     if ((long long)g.nx * g.ny >= LBM_STEP_PAIRS_LARGE_16_MIN) switch (prec) {
       case PREC_F16: return launch_step2_t<L, COLL, __half>(fin, fout, g, pd, st, err);
