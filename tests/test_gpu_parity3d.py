@@ -190,7 +190,8 @@ def test_shear_wave_decays_at_nu_k2(name):
 
 
 @pytest.mark.parametrize("bc", [(0, 0, 0), (0, 1, 1)])
-@pytest.mark.parametrize("storage,nx", [("f64", 8), ("f64", 264), ("f32", 520), ("f16", 520)])
+@pytest.mark.parametrize("storage,nx", [("f64", 8), ("f64", 264), ("f32", 520), ("f16", 520), ("bf16", 520),
+                                        ("i16", 520)])
 @pytest.mark.parametrize("name", ["D3Q19", "D3Q27", "D3V39"])
 def test_staged_tiles_and_wraps(name, storage, nx, bc):
     """Grids periodic in x with whole 16-byte rows take the staged kernel: a row that fits one tile (nx = 8)
@@ -210,9 +211,10 @@ def test_staged_tiles_and_wraps(name, storage, nx, bc):
         assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-12
     elif storage == "f32":
         assert pop_rel(got, ref, o.lattice(name).w) <= 3 * TOL["f32"]
-    else:  # three roundings to binary16 of the shifted deviation: as the one-step bound, three times
+    else:  # three roundings to the 16-bit format of the shifted deviation: the one-step bound, three times
         w = o.lattice(name).w[:, None, None, None]
-        assert np.max(np.abs(got - ref) / w) <= 3 * 2e-3 * np.abs(f / w - 1.0).max()
+        tol16 = {"f16": 2e-3, "bf16": 2e-2, "i16": 2e-3}[storage]
+        assert np.max(np.abs(got - ref) / w) <= 3 * tol16 * np.abs(f / w - 1.0).max()
 
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
