@@ -48,21 +48,75 @@ struct Storages3 {
   static constexpr bool SIXTEEN_BIT = L::Q < 100;
 };
 
-// One thread per cell; a block is STEP_BX consecutive x of one (y, z) row.  Rows at least VMAX away from
-// the y and z edges (block-uniform) take one load sequence with the x wrap folded into a base pointer per
-// x-velocity; the other rows (and grids narrower than the stencil) the general path.
-template <class L, int COLL, class Real, class S>
+// Rows of the direct kernel: interior rows (at least VMAX away from the y and z faces, nx >= VMAX) and the
+// others.  On large grids each class runs in a launch of its own, so that neither kernel carries the
+// other's load sequence (the two together overflowed the instruction cache on D3Q103: 74 % of the stall
+// samples were no_instruction); where edge rows are more than an eighth of the grid, the second launch
+// would be a fraction of a wave and one launch of the kernel with both sequences is faster (D3Q103 FP32:
+// 256^3, 4.7 % edge rows, split 5.14 -> 5.46 GLUPS; 128 x 64 x 64, 18 %, combined 2.43, split 1.99, the
+// general sequence alone 0.97).
+struct Rows3 {
+  int interior;     // count of interior rows; 0 = one launch over every row (ROWS_ALL)
+  int ny_in;        // interior rows per plane
+  long long edge;   // count of edge rows
+};
+constexpr int ROWS_ALL = 0, ROWS_INTERIOR = 1, ROWS_EDGE = 2;
+
+template <int V>
+__host__ __device__ inline Rows3 rows3(const Geom3& g) {
+  Rows3 r{};
+  const long long all = (long long)g.ny * g.nz;
+  if (g.ny > 2 * V && g.nz > 2 * V && g.nx >= V) {
+    r.ny_in = g.ny - 2 * V;
+    r.interior = r.ny_in * (g.nz - 2 * V);
+    r.edge = (long long)2 * V * g.ny + (long long)(g.nz - 2 * V) * 2 * V;
+    if (8 * r.edge > all) r = Rows3{0, 0, 0};
+  }
+  return r;
+}
+
+// Edge row e -> (y, z): the 2 V planes nearest the z faces whole, then 2 V rows of every other plane.
+template <int V>
+__device__ __forceinline__ void edge_row(const Geom3& g, long long e, int& y, int& z) {
+  if (e < (long long)2 * V * g.ny) {
+    const int k = (int)(e / g.ny);
+    y = (int)(e - (long long)k * g.ny);
+    z = k < V ? k : g.nz - 2 * V + k;
+  } else {
+    const long long e2 = e - (long long)2 * V * g.ny;
+    const int k = (int)(e2 % (2 * V));
+    z = V + (int)(e2 / (2 * V));
+    y = k < V ? k : g.ny - 2 * V + k;
+  }
+}
+
+// One thread per cell; a block is STEP_BX consecutive x of one (y, z) row.  Interior rows take one load
+// sequence with the x wrap folded into a base pointer per x-velocity; edge rows (and grids thinner than the
+// stencil) the general per-population source coordinates.  ROWS selects the rows of a launch.
+template <class L, int COLL, class Real, class S, int ROWS>
 __global__ void __launch_bounds__(STEP_BX, Step3Blocks<L, Real>::MIN)
-    k_step3(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, CollParams<Real> P,
+    k_step3(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, Rows3 rows, CollParams<Real> P,
             const __grid_constant__ PullOffsets3<L::Q> off) {
-  const int row = blockIdx.x / nbx;
-  const int bx = blockIdx.x - row * nbx;
-  const int y = row % g.ny, z = row / g.ny;
+  const int rb = blockIdx.x / nbx;
+  const int bx = blockIdx.x - rb * nbx;
+  int y, z;
+  if constexpr (ROWS == ROWS_EDGE) {
+    edge_row<L::VMAX>(g, rb, y, z);
+  } else if constexpr (ROWS == ROWS_INTERIOR) {
+    z = L::VMAX + rb / rows.ny_in;
+    y = L::VMAX + (rb - (rb / rows.ny_in) * rows.ny_in);
+  } else {
+    y = rb % g.ny;
+    z = rb / g.ny;
+  }
   const int x = bx * STEP_BX + threadIdx.x;
   if (x >= g.nx) return;
   const long long cen = (long long)z * g.plane + (long long)y * g.pitch + x;
   Real q[L::Q];
-  if (y >= L::VMAX && y + L::VMAX < g.ny && z >= L::VMAX && z + L::VMAX < g.nz && g.nx >= L::VMAX) {
+  const bool interior = ROWS == ROWS_INTERIOR ||
+                        (ROWS == ROWS_ALL && y >= L::VMAX && y + L::VMAX < g.ny && z >= L::VMAX &&
+                         z + L::VMAX < g.nz && g.nx >= L::VMAX);
+  if (ROWS != ROWS_EDGE && interior) {
     const char* c = reinterpret_cast<const char*>(fin + cen);
     const char* cb[2 * L::VMAX + 1];
     sfor<0, 2 * L::VMAX + 1>([&](auto J) {
@@ -325,10 +379,21 @@ inline cudaError_t launch_step3_t(const void* fin, void* fout, const Geom3& g, c
     return cudaGetLastError();
   }
   const int nbx = (g.nx + STEP_BX - 1) / STEP_BX;
-  const long long nblocks = (long long)nbx * g.ny * g.nz;
-  if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_step3<L, COLL, Real, S><<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
-                                                                    cast_params<Real>(pd), off);
+  const Rows3 rows = rows3<L::VMAX>(g);
+  const CollParams<Real> P = cast_params<Real>(pd);
+  if (rows.interior == 0) {
+    const long long nb = (long long)nbx * g.ny * g.nz;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_step3<L, COLL, Real, S, ROWS_ALL><<<(unsigned)nb, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, rows, P,
+                                                                        off);
+    return cudaGetLastError();
+  }
+  const long long nb_in = (long long)nbx * rows.interior, nb_edge = (long long)nbx * rows.edge;
+  if (nb_in > 0x7fffffffLL || nb_edge > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_step3<L, COLL, Real, S, ROWS_INTERIOR><<<(unsigned)nb_in, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
+                                                                                rows, P, off);
+  k_step3<L, COLL, Real, S, ROWS_EDGE><<<(unsigned)nb_edge, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, rows,
+                                                                            P, off);
   return cudaGetLastError();
 }
 
