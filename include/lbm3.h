@@ -62,10 +62,11 @@ void lbm3_destroy(lbm3_ctx *c);
  * arrays go through a device work area of 104 B per cell allocated on first use. */
 int lbm3_init(lbm3_ctx *c, const double *rho, const double *u, const double *grad, int on_device);
 
-/* n >= 0 time steps: pull streaming then collision, one fused kernel per step, double-buffered.
+/* n >= 0 time steps: pull streaming then collision fused in one pass per step, double-buffered.
  * Enqueued on the context's stream; does not synchronize.  Grids periodic in x with nx a multiple of
  * 16 bytes' worth of cells run the staged kernel (populations brought to shared memory by asynchronous
- * bulk copies a few row tiles ahead); the others the direct-load kernel.  Both compute the same step. */
+ * bulk copies a few row tiles ahead; D3Q103 excepted); the others the direct-load kernel, in one launch, or
+ * on large grids two (the rows near the y and z faces separately).  All compute the same step. */
 int lbm3_step(lbm3_ctx *c, int n);
 
 /* rho [cells] and u [3][cells] of the current state; either may be NULL. */
