@@ -7,7 +7,10 @@ D2V17 (3rd order) and D2V37 (4th order), RR collision, FP32 compute and FP32
 storage.  One bench step = one lbm_step on each of the three lattices.
 `value` is the aggregate GLUPS (cells updated per second, all lattices, all
 ranks); per-lattice GLUPS, HBM roofline fractions and the low-precision
-(shifted FP16 / BF16) and FP64 variants are reported alongside.
+(shifted FP16 / BF16) and FP64 variants are reported alongside, with further
+sections (4096^2 grids, finite-difference a1, accuracy, batched sweep, learned
+closure, stability map, and the 3D lattices of Tab. II on a 256^3 Taylor-Green
+vortex) after the timed headline steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
