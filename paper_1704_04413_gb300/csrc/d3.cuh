@@ -77,7 +77,7 @@ __host__ __device__ inline Rows3 rows3(const Geom3& g) {
 
 // Edge row e -> (y, z): the 2 V planes nearest the z faces whole, then 2 V rows of every other plane.
 template <int V>
-__device__ __forceinline__ void edge_row(const Geom3& g, long long e, int& y, int& z) {
+__host__ __device__ __forceinline__ void edge_row(const Geom3& g, long long e, int& y, int& z) {
   if (e < (long long)2 * V * g.ny) {
     const int k = (int)(e / g.ny);
     y = (int)(e - (long long)k * g.ny);
