@@ -73,7 +73,8 @@ def shear_wave(nx: int, ny: int, amplitude: float, mode: int = 1) -> Fields:
 
 def taylor_green_3d_box(nx: int, ny: int, nz: int, u0: float):
     """The Taylor-Green vortex of taylor_green_3d on an nx x ny x nz periodic box (wavenumber 2 pi / n per
-    axis); same layout of the returned arrays."""
+    axis), u_y scaled by kx / ky so that the field stays divergence-free; same layout of the returned arrays
+    (equal to taylor_green_3d on a cube)."""
     kx, ky, kz = 2.0 * np.pi / nx, 2.0 * np.pi / ny, 2.0 * np.pi / nz
     X = np.arange(nx, dtype=np.float64)[None, None, :] * kx
     Y = np.arange(ny, dtype=np.float64)[None, :, None] * ky
@@ -81,15 +82,16 @@ def taylor_green_3d_box(nx: int, ny: int, nz: int, u0: float):
     shape = (nz, ny, nx)
     sx, cx, sy, cy, sz, cz = np.sin(X), np.cos(X), np.sin(Y), np.cos(Y), np.sin(Z), np.cos(Z)
     u = np.zeros((3,) + shape)
+    r = kx / ky
     u[0] = u0 * sx * cy * cz
-    u[1] = -u0 * cx * sy * cz
+    u[1] = -u0 * r * cx * sy * cz
     g = np.zeros((9,) + shape)
     g[0] = u0 * kx * cx * cy * cz
     g[1] = -u0 * ky * sx * sy * cz
     g[2] = -u0 * kz * sx * cy * sz
-    g[3] = u0 * kx * sx * sy * cz
-    g[4] = -u0 * ky * cx * cy * cz
-    g[5] = u0 * kz * cx * sy * sz
+    g[3] = u0 * r * kx * sx * sy * cz
+    g[4] = -u0 * r * ky * cx * cy * cz
+    g[5] = u0 * r * kz * cx * sy * sz
     return np.ones(shape), u, g
 
 
