@@ -344,20 +344,29 @@ static double tau_of_order(const orc_params *p, int n) {
 /*  PR/RR rebuild (Eq. GenRegCollision with one relaxation time per order,   */
 /*      Sec. II.B): f* = f^(0) + sum_n (1 - 1/tau_n) f^(1,n), tau_2 = tau.   */
 /* ------------------------------------------------------------------------ */
-static int collide_cell(const orc_params *p, const double *f_in, const double *grad, double *f_out);
+static int collide_cell(const orc_params *p, const double *f_in, const double *grad, const double *delta,
+                        double *f_out);
 
 int orc_collide(const orc_params *p, const double *f_in, double *f_out) {
   if (p->a1_source != 0) return -1;
-  return collide_cell(p, f_in, NULL, f_out);
+  return collide_cell(p, f_in, NULL, NULL, f_out);
 }
 
 int orc_collide_fd(const orc_params *p, const double *f_in, const double *grad, double *f_out) {
   if (p->a1_source != 1 || !grad) return -1;
-  return collide_cell(p, f_in, grad, f_out);
+  return collide_cell(p, f_in, grad, NULL, f_out);
 }
 
-/* grad == NULL: a1 by projection; else a1^(2) (and the thermal temperature gradients) from grad. */
-static int collide_cell(const orc_params *p, const double *f_in, const double *grad, double *f_out) {
+int orc_collide_delta(const orc_params *p, const double *f_in, const double *delta, double *f_out) {
+  if (p->a1_source != 0 || p->collision != ORC_RR || p->thermal || !delta) return -1;
+  return collide_cell(p, f_in, NULL, delta, f_out);
+}
+
+/* grad == NULL: a1 by projection; else a1^(2) (and the thermal temperature gradients) from grad.
+ * delta != NULL (isothermal RR, projection): delta[0..2] = (xx, xy, yy) is added to the projected a1^(2)
+ * (both xy and yx entries) before the recursion builds the higher orders. */
+static int collide_cell(const orc_params *p, const double *f_in, const double *grad, const double *delta,
+                        double *f_out) {
   orc_lattice L;
   if (orc_lattice_get(p->lattice, &L)) return -1;
   int neq, nreg;
@@ -407,6 +416,12 @@ static int collide_cell(const orc_params *p, const double *f_in, const double *g
     orc_a1_recursive(L.cs2, rho, ux, uy, theta, p->thermal, nreg, a0, a1);
   } else if (p->collision == ORC_RR) {
     for (int t = 0; t < 4; t++) TEN(a1, 2, t) = TEN(a1p, 2, t);
+    if (delta) {
+      TEN(a1, 2, pair_tuple(0, 0)) += delta[0];
+      TEN(a1, 2, pair_tuple(0, 1)) += delta[1];
+      TEN(a1, 2, pair_tuple(1, 0)) += delta[1];
+      TEN(a1, 2, pair_tuple(1, 1)) += delta[2];
+    }
     if (p->thermal) {
       if (nreg >= 3) {
         /* the projected a1^(3) is needed whatever nreg: project it here if nreg == 3 did not */
@@ -510,7 +525,7 @@ int orc_step(const orc_params *p, const double *f_in, double *f_out) {
     for (int x = 0; x < p->nx; x++) {
       gather_cell(p, &L, f_in, x, y, fc);
       if (m) central_gradients(p, m, x, y, grad);
-      err |= collide_cell(p, fc, m ? grad : NULL, fo) != 0;
+      err |= collide_cell(p, fc, m ? grad : NULL, NULL, fo) != 0;
       for (int i = 0; i < L.V; i++) f_out[i * plane + (long long)y * p->nx + x] = fo[i];
     }
   }
@@ -536,9 +551,33 @@ int orc_step_cells(const orc_params *p, const double *f_in, int ncell, const lon
     int x = (int)(cells[k] % p->nx), y = (int)(cells[k] / p->nx);
     gather_cell(p, &L, f_in, x, y, fc);
     if (m) central_gradients(p, m, x, y, grad);
-    err |= collide_cell(p, fc, m ? grad : NULL, f_out + (long long)k * L.V) != 0;
+    err |= collide_cell(p, fc, m ? grad : NULL, NULL, f_out + (long long)k * L.V) != 0;
   }
   free(m);
+  return err ? -1 : 0;
+}
+
+/* One step (pull streaming + RR collision) with a per-cell correction of a1^(2): delta[3][ny][nx] holds the
+ * (xx, xy, yy) components added at each cell (orc_collide_delta). */
+int orc_step_delta(const orc_params *p, const double *f_in, const double *delta, double *f_out) {
+  orc_lattice L;
+  if (orc_lattice_get(p->lattice, &L)) return -1;
+  int neq, nreg;
+  if (resolve_orders(p, &L, &neq, &nreg)) return -1;
+  if (p->a1_source != 0 || p->collision != ORC_RR || p->thermal || !delta) return -1;
+  long long plane = (long long)p->nx * p->ny;
+  int err = 0;
+#pragma omp parallel for schedule(static) reduction(| : err)
+  for (int y = 0; y < p->ny; y++) {
+    double fc[ORC_MAXQ], fo[ORC_MAXQ];
+    for (int x = 0; x < p->nx; x++) {
+      long long c = (long long)y * p->nx + x;
+      const double d[3] = {delta[c], delta[plane + c], delta[2 * plane + c]};
+      gather_cell(p, &L, f_in, x, y, fc);
+      err |= collide_cell(p, fc, NULL, d, fo) != 0;
+      for (int i = 0; i < L.V; i++) f_out[i * plane + c] = fo[i];
+    }
+  }
   return err ? -1 : 0;
 }
 

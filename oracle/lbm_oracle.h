@@ -108,12 +108,21 @@ int orc_collide(const orc_params *p, const double *f_in, double *f_out);
  * and, thermal, mu cs^2 d_g theta = tau_3 rho cs^4 theta d_g theta in place of Eq. TempGradLBM. */
 int orc_collide_fd(const orc_params *p, const double *f_in, const double *grad, double *f_out);
 
+/* Isothermal RR collision of one cell with a correction of the non-equilibrium stress: delta[3] =
+ * (xx, xy, yy) is added to the projected a1^(2) (xy to both off-diagonal entries), and the higher orders
+ * follow by Eq. (MalaspinasRecursiveRelation) from the corrected a1^(2).  -1 unless RR, isothermal,
+ * a1 by projection. */
+int orc_collide_delta(const orc_params *p, const double *f_in, const double *delta, double *f_out);
+
 /* One full step (pull streaming + collision) on f_in[V][ny][nx] -> f_out. */
 int orc_step(const orc_params *p, const double *f_in, double *f_out);
 
 /* Pull streaming + collision only at the listed cells (cell = y*nx + x);
  * f_out is [ncell][V]. */
 int orc_step_cells(const orc_params *p, const double *f_in, int ncell, const long long *cells, double *f_out);
+
+/* One step with orc_collide_delta at every cell, delta[3][ny][nx]. */
+int orc_step_delta(const orc_params *p, const double *f_in, const double *delta, double *f_out);
 
 /* Initial populations f^(0),N (+ f^(1) from analytic velocity gradients when
  * grad_u != NULL; grad_u is [4][ny][nx] = dux/dx, dux/dy, duy/dx, duy/dy).

@@ -178,6 +178,37 @@ def step_cells(p: OrcParams, f: np.ndarray, cells: np.ndarray) -> np.ndarray:
     return out
 
 
+def collide_delta(p: OrcParams, f: np.ndarray, delta) -> np.ndarray:
+    """One cell's isothermal RR collision with (xx, xy, yy) = delta added to the projected a1^(2) before the
+    recursion (Eq. MalaspinasRecursiveRelation builds the higher orders from the corrected a1^(2))."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    out = np.empty_like(f)
+    if lib().orc_collide_delta(ctypes.byref(p), _dp(f), _dp(d), _dp(out)) != 0:
+        raise ValueError("orc_collide_delta rejected the parameters")
+    return out
+
+
+def step_delta(p: OrcParams, f: np.ndarray, delta: np.ndarray) -> np.ndarray:
+    """One step whose collision adds delta[3][ny][nx] = (xx, xy, yy) to each cell's projected a1^(2)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    if d.shape != (3, p.ny, p.nx):
+        raise ValueError("delta must be [3][ny][nx]")
+    out = np.empty_like(f)
+    if lib().orc_step_delta(ctypes.byref(p), _dp(f), _dp(d), _dp(out)) != 0:
+        raise ValueError("orc_step_delta rejected the parameters")
+    return out
+
+
+def closure_delta(y: np.ndarray, u0: float, tau: float, nx: int, ny: int) -> np.ndarray:
+    """The learned closure's correction of a1^(2) from the network outputs y[nx*ny][>=3] (the subgrid stress
+    (xx, xy, yy) / u0^2): Delta a1^(2) = u0^2 y / (1 - 1/tau), so that the relaxed non-equilibrium part
+    (1 - 1/tau) a1^(2) of the post-collision state carries the predicted stress.  Returned as [3][ny][nx]."""
+    y = np.asarray(y, dtype=np.float64)[:, :3]
+    return (u0 * u0 * y / (1.0 - 1.0 / tau)).T.reshape(3, ny, nx)
+
+
 def init(p: OrcParams, rho, ux, uy, T=None, grad_u=None) -> np.ndarray:
     V = lattice(p.lattice).V
     c = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
