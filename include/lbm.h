@@ -149,6 +149,21 @@ int lbm_set_populations(lbm_ctx *c, const double *f, int on_device);
 /* Number of steps since the last lbm_init / lbm_set_populations / lbm_load. */
 long long lbm_step_count(const lbm_ctx *c);
 
+/* Testing hook for the failure path of the staged step kernels (D2Q9 / D2V17
+ * with binary16 or bfloat16 storage on x-periodic grids whose rows are whole
+ * 16-byte units; other contexts never run them and ignore the hook).  Those
+ * kernels copy population rows into shared memory asynchronously and wait for
+ * the copies with a time limit; a wait that runs out records LBM_ETIMEOUT in
+ * the context, which lbm_conservation / lbm_diagnostics then return.  With
+ * block >= 0, the producer of that thread block announces the copies of its
+ * last tile but does not issue them, so that block's compute warps give up
+ * after wait_seconds (every earlier copy has been consumed, so none is in
+ * flight when the block ends); block = -1 turns the hook off.  wait_seconds
+ * (0 < w <= 10) replaces the default limit of 1 s for every wait of the
+ * context's staged launches.  No counterpart in the paper.  LBM_EINVAL on bad
+ * arguments. */
+int lbm_test_inject_copy_fault(lbm_ctx *c, int block, double wait_seconds);
+
 /* The relaxation time tau actually used (derived from nu when tau <= 0). */
 double lbm_tau(const lbm_ctx *c);
 
@@ -182,16 +197,21 @@ int lbm_load(lbm_ctx *c, const char *path);
  * address up (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  All calls share the array: calls that
  * overlap on the GPU (other streams, other threads) race and must be ordered
- * by the caller.  Errors: LBM_EINVAL (bad argument or size), LBM_ECUDA. */
+ * by the caller.  The address is looked up once per device and kept: a
+ * cudaDeviceReset of that device after its first call is not supported (the
+ * module, and with it the array, may be reloaded elsewhere).  f and out4 must
+ * be device (or managed) memory: host addresses return LBM_EINVAL; the sizes
+ * of the buffers cannot be checked here.  Errors: LBM_EINVAL (bad argument,
+ * size or pointer kind), LBM_ECUDA. */
 #define LBM_NOALLOC_MAX_CELLS 16777216LL
 int lbm_conservation_noalloc(int lattice, int storage, const void *f, int nx, int ny, int pitch, double rho0,
                              double store_scale, double *out4, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched sweep: up to LBM_BATCH_MAX independent D2Q9 / D2V17 grids of any
- * sizes and relaxation times, advanced together by one kernel launch per
- * lattice per time step (one launch when all instances share a lattice; the
- * launches recorded once in a CUDA graph and replayed).  Per cell the arithmetic is that of lbm_step, so a batched step
+ * sizes and relaxation times, mixed freely, advanced together by one kernel
+ * launch per time step (recorded once in a CUDA graph of two steps and
+ * replayed).  Per cell the arithmetic is that of lbm_step, so a batched step
  * is bit-identical to stepping each instance on its own.
  * ------------------------------------------------------------------------ */
 #define LBM_BATCH_MAX 64

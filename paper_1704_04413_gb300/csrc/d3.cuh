@@ -17,6 +17,8 @@ struct Geom3 {
   int nx, ny, nz;
   int bc[3];          // BC_PERIODIC / BC_ZERO_GRADIENT per axis
   int* status;        // device word: nonzero after a staged step kernel gave up waiting on its copies
+  unsigned long long wait_ns;  // limit of the staged kernels' bounded waits (kBulkWaitNs by default)
+  int fault_block;     // test hook: this block's producer announces but never issues its last tile's copies
 };
 
 template <int Q>
@@ -238,8 +240,11 @@ __global__ void __launch_bounds__(Stage3<L, S>::THREADS, Staged3Blocks<L, S>::MI
     bool ok = true;
     for (; k < n_mine; ++k, tw.next(nbx, g.ny)) {
       const int s = k % NS;
-      if (k >= NS) ok = mbar_wait(&empty[s], (uint32_t)(((k / NS) + 1) & 1));
+      if (k >= NS) ok = mbar_wait(&empty[s], (uint32_t)(((k / NS) + 1) & 1), g.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) break;
+      // test hook: the last tile's copies are announced but not issued (every earlier stage has been
+      // consumed, so no copy is in flight when the block ends)
+      const bool skip = (int)blockIdx.x == g.fault_block && k == n_mine - 1;
       const int y = tw.y, z = tw.z;
       const int x0 = tw.bx * St::BXT;
       const int xa = max(x0 - St::PAD, 0), xb = min(x0 + St::BXT + St::PAD, g.nx);
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(Stage3<L, S>::THREADS, Staged3Blocks<L, S>::MI
       __syncwarp();
       unsigned char* st = sm + (size_t)s * St::STAGE_BYTES;
       const char* base = reinterpret_cast<const char*>(fin);
-      for (int i = lane; i < L::Q; i += 32) {  // one population per lane
+      for (int i = lane; i < L::Q && !skip; i += 32) {  // one population per lane
         const int ys = src_coord(y, off.cy[i], g.ny, g.bc[1]);
         const int zs = src_coord(z, off.cz[i], g.nz, g.bc[2]);
         const char* src =
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(Stage3<L, S>::THREADS, Staged3Blocks<L, S>::MI
       if (lane == 0) {
         atomicExch(g.status, 1);
         for (int j = 1; j <= NS; ++j)
-          if (k - j >= 0) mbar_wait(&full[(k - j) % NS], (uint32_t)(((k - j) / NS) & 1));
+          if (k - j >= 0) mbar_wait(&full[(k - j) % NS], (uint32_t)(((k - j) / NS) & 1), g.wait_ns);
       }
     }
     return;
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(Stage3<L, S>::THREADS, Staged3Blocks<L, S>::MI
   TileWalk tw(t_begin, nbx, g.ny);
   for (int k = 0; k < n_mine; ++k, tw.next(nbx, g.ny)) {
     const int s = k % NS;
-    if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((k / NS) & 1)))) {
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (uint32_t)((k / NS) & 1), g.wait_ns))) {
       // the copies of this tile did not arrive: flag it and stop (the producer then gives up on this stage)
       if (lane == 0) atomicExch(g.status, 1);
       return;
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(FB3) k_set_plane3(S* __restrict__ f, Geom3 g, 
 }
 
 // FP64 mass and momentum: each block sums a fixed range of cells in a fixed order into partials[4][block];
-// k_sum_partials3 then adds the partials in block order (deterministic, two passes).
+// k_sum_partials3 then adds the partials in an order fixed by their count (deterministic, two passes).
 template <class L, class S>
 __global__ void __launch_bounds__(FB3) k_conservation3(const S* __restrict__ f, Geom3 g, double rho0, double inv_s,
                                                        long long per_block, double* __restrict__ partials) {
@@ -606,13 +611,32 @@ __global__ void __launch_bounds__(FB3) k_conservation3(const S* __restrict__ f, 
   if (threadIdx.x == 0)
     for (int k = 0; k < 4; ++k) partials[(long long)k * gridDim.x + blockIdx.x] = sh[k][0];
 }
+// Second pass: one block of SUM3_T threads, thread t adding the partials t, t + SUM3_T, ... of each component
+// (coalesced), then a shuffle tree and the warps in order; the addition order depends on nblocks alone.
+constexpr int SUM3_T = 256;
 template <int K>
-__global__ void k_sum_partials3(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
-  const int k = threadIdx.x;
-  if (k >= K) return;
-  double a = 0.0;
-  for (int b = 0; b < nblocks; ++b) a += partials[(long long)k * nblocks + b];
-  out[k] = a;
+__global__ void __launch_bounds__(SUM3_T) k_sum_partials3(const double* __restrict__ partials, int nblocks,
+                                                         double* __restrict__ out) {
+  __shared__ double sh[SUM3_T / 32][K];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  double a[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) a[k] = 0.0;
+  for (int b = t; b < nblocks; b += SUM3_T)
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] += partials[(long long)k * nblocks + b];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    if (lane == 0) sh[wid][k] = a[k];
+  }
+  __syncthreads();
+  if (t < K) {
+    double r = 0.0;
+    for (int w = 0; w < SUM3_T / 32; ++w) r += sh[w][t];
+    out[t] = r;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -702,7 +726,7 @@ struct Ops3 {
     return with_storage<L>(prec, [&](auto tag) {
       using S = decltype(tag);
       k_conservation3<L, S><<<nblocks, FB3, 0, st>>>((const S*)f, g, rho0, inv_s, per_block, partials);
-      k_sum_partials3<4><<<1, 32, 0, st>>>(partials, nblocks, out4);
+      k_sum_partials3<4><<<1, SUM3_T, 0, st>>>(partials, nblocks, out4);
       return cudaGetLastError();
     });
   }

@@ -146,7 +146,7 @@ __global__ void k_set_plane(S* __restrict__ f, StepGeom g, int i, double rho0, d
 // ---------------------------------------------------------------------------
 // Deterministic reductions: a fixed per-thread order, a warp-shuffle tree and
 // a fixed-order block tree give per-block partials; one block then adds the
-// partials in index order.
+// partials in an order fixed by their count (k_sum_partials).
 // ---------------------------------------------------------------------------
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double* partial_out) {
@@ -192,13 +192,32 @@ __global__ void k_conservation_partials(const S* __restrict__ f, StepGeom g, dou
   block_sum<4>(v, partials + 4LL * blockIdx.x);
 }
 
-__global__ void k_sum_partials(const double* __restrict__ partials, int nblocks, int k_per, double* __restrict__ out) {
-  // one block; thread k adds component k of every partial in index order
-  const int k = threadIdx.x;
-  if (k >= k_per) return;
-  double a = 0.0;
-  for (int b = 0; b < nblocks; ++b) a += partials[(long long)b * k_per + k];
-  out[k] = a;
+// Second pass of the two-pass sums: one block of SUM_T threads.  Thread t adds the partials t, t + SUM_T,
+// t + 2 SUM_T, ... (coalesced), then the threads' sums are combined by a warp shuffle tree and the warps'
+// sums in warp order.  The order of every addition is fixed by nblocks alone, so the result is the same
+// bits on every run.
+constexpr int SUM_T = 256;
+__global__ void __launch_bounds__(SUM_T) k_sum_partials(const double* __restrict__ partials, int nblocks, int k_per,
+                                                       double* __restrict__ out) {
+  __shared__ double sh[SUM_T / 32][4];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = t; b < nblocks; b += SUM_T)
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < k_per) a[k] += partials[(long long)b * k_per + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    if (lane == 0) sh[wid][k] = a[k];
+  }
+  __syncthreads();
+  if (t < k_per) {
+    double r = 0.0;
+    for (int w = 0; w < SUM_T / 32; ++w) r += sh[w][t];
+    out[t] = r;
+  }
 }
 
 // u^2 and enstrophy density omega^2 / 2 with fourth-order centred differences (Sec. III.B)
@@ -322,7 +341,7 @@ static cudaError_t cons_t(const void* f, const StepGeom& g, double rho0, double 
                           double* out4, cudaStream_t st) {
   const unsigned nb_ = nblk(g);
   k_conservation_partials<L, S><<<nb_, FB, 0, st>>>((const S*)f, g, rho0, inv_s, partials);
-  k_sum_partials<<<1, 32, 0, st>>>(partials, (int)nb_, 4, out4);
+  k_sum_partials<<<1, SUM_T, 0, st>>>(partials, (int)nb_, 4, out4);
   return cudaGetLastError();
 }
 template <class L>
@@ -367,6 +386,6 @@ cudaError_t lbm_launch_diagnostics(const double* ux, const double* uy, const Ste
                                    double* out4, cudaStream_t st) {
   const unsigned nb_ = nblk(g);
   k_diag_partials<<<nb_, FB, 0, st>>>(ux, uy, g, partials);
-  k_sum_partials<<<1, 32, 0, st>>>(partials, (int)nb_, 4, out4);
+  k_sum_partials<<<1, SUM_T, 0, st>>>(partials, (int)nb_, 4, out4);
   return cudaGetLastError();
 }

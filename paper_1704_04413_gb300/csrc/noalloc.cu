@@ -44,6 +44,18 @@ int partials_for_current_device(double** out) {
   return LBM_OK;
 }
 
+// True when p is memory a kernel on the current device may read and write: device or managed memory.
+// Host memory (pageable or pinned) is refused, so that a host address passed by mistake returns
+// LBM_EINVAL instead of reaching the kernel.
+bool device_accessible(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error the failed query recorded
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 bool is_pow2(double s) {
   if (!(s > 0)) return false;
   int e = 0;
@@ -69,6 +81,7 @@ extern "C" int lbm_conservation_noalloc(int lattice, int storage, const void* f,
   const double r0 = rho0 == 0 ? 1.0 : rho0;
   const double s = store_scale == 0 ? 1.0 : store_scale;
   if (!(r0 > 0) || !is_pow2(s)) return LBM_EINVAL;
+  if (!device_accessible(f) || !device_accessible(out4)) return LBM_EINVAL;
   double* partials = nullptr;
   const int rc = partials_for_current_device(&partials);
   if (rc != LBM_OK) return rc;
