@@ -73,9 +73,9 @@ int lbm3_step(lbm3_ctx *c, int n);
 int lbm3_moments(lbm3_ctx *c, double *rho, double *u, int on_device);
 
 /* FP64 domain sums: out[0] mass, out[1..3] momentum.  Deterministic (fixed-order two-pass reduction);
- * synchronizes; LBM_EUNSTABLE (sums still written) when a sum is not finite; LBM_ECUDA when a step kernel
- * gave up waiting (1 s) on its own asynchronous copies since the context was created (not expected: the
- * word exists so that no wait is unbounded). */
+ * synchronizes; LBM_EUNSTABLE (sums still written) when a sum is not finite; LBM_ETIMEOUT when a step
+ * kernel gave up waiting (1 s unless lbm3_test_inject_copy_fault shortened it) on its own asynchronous
+ * copies since the context was created (not expected: the word exists so that no wait is unbounded). */
 int lbm3_conservation(lbm3_ctx *c, double out[4]);
 
 /* Decoded populations f[V][nz][ny][nx] (library velocity order), and the inverse (encodes into the
@@ -86,6 +86,13 @@ int lbm3_set_populations(lbm3_ctx *c, const double *f, int on_device);
 
 /* The relaxation time tau-bar in use. */
 double lbm3_tau(const lbm3_ctx *c);
+
+/* Testing hook for the staged kernel's failure path, as lbm_test_inject_copy_fault in lbm.h: with
+ * block >= 0 that thread block's producer announces the copies of its last tile but does not issue them,
+ * so its compute warps' wait runs out after wait_seconds (0 < w <= 10, the limit of every wait of the
+ * context's staged launches; default 1 s) and lbm3_conservation returns LBM_ETIMEOUT; block = -1 turns
+ * it off.  Contexts that do not run the staged kernel ignore it.  No counterpart in the paper. */
+int lbm3_test_inject_copy_fault(lbm3_ctx *c, int block, double wait_seconds);
 
 #ifdef __cplusplus
 }

@@ -77,13 +77,13 @@ cudaError_t lbm_ctx_launch_step(lbm_ctx* c, const void* fin, void* fout) {
   const CollParamsD pd = lbm_ctx_coll_params(c);
   const int coll = c->p.collision;
   switch (c->p.lattice) {
-    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st);
+    case LBM_D2Q9: return lbm_launch_step_d2q9(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, &c->ctl, c->st);
     case LBM_D2V17:
-      return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st);
+      return lbm_launch_step_d2v17(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, &c->ctl, c->st);
     case LBM_D2V37:
       return c->p.thermal
-                 ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st)
-                 : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, c->dev_err, c->st);
+                 ? lbm_launch_step_d2v37_thermal(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, &c->ctl, c->st)
+                 : lbm_launch_step_d2v37(coll, c->prec, fin, fout, c->g, pd, c->fd_mom, &c->ctl, c->st);
   }
   return cudaErrorInvalidValue;
 }
@@ -233,7 +233,17 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     lbm_destroy(c);
     return LBM_ECUDA;
   }
+  c->ctl.status = c->dev_err;
+  c->ctl.wait_ns = lbm::kBulkWaitNs;
+  c->ctl.fault_block = -1;
   *out = c;
+  return LBM_OK;
+}
+
+int lbm_test_inject_copy_fault(lbm_ctx* c, int block, double wait_seconds) {
+  if (!c || block < -1 || !(wait_seconds > 0) || wait_seconds > 10.0) return LBM_EINVAL;
+  c->ctl.fault_block = block;
+  c->ctl.wait_ns = (unsigned long long)(wait_seconds * 1e9);
   return LBM_OK;
 }
 

@@ -191,6 +191,8 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
   }
   // out4[4] holds the status word of the staged step kernels (0 = every copy wait completed)
   c->g.status = reinterpret_cast<int*>(c->out4 + 4);
+  c->g.wait_ns = lbm::kBulkWaitNs;
+  c->g.fault_block = -1;
   // padding columns are never read by a kernel; clear them once so transfers are deterministic
   if (cudaMemsetAsync(c->buf[0], 0, bytes, c->st) != cudaSuccess ||
       cudaMemsetAsync(c->buf[1], 0, bytes, c->st) != cudaSuccess ||
@@ -208,6 +210,13 @@ int lbm3_create(const lbm3_params* p, lbm3_ctx** out) {
 extern "C" {
 
 double lbm3_tau(const lbm3_ctx* c) { return c ? c->tau : 0.0; }
+
+int lbm3_test_inject_copy_fault(lbm3_ctx* c, int block, double wait_seconds) {
+  if (!c || block < -1 || !(wait_seconds > 0) || wait_seconds > 10.0) return LBM_EINVAL;
+  c->g.fault_block = block;
+  c->g.wait_ns = (unsigned long long)(wait_seconds * 1e9);
+  return LBM_OK;
+}
 
 int lbm3_init(lbm3_ctx* c, const double* rho, const double* u, const double* grad, int on_device) {
   if (!c || !rho || !u) return LBM_EINVAL;
@@ -269,7 +278,7 @@ int lbm3_conservation(lbm3_ctx* c, double out[4]) {
                                c->out4, c->st));
   LBM3_CK(cudaMemcpyAsync(c->host4, c->out4, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   LBM3_CK(cudaStreamSynchronize(c->st));
-  if (*reinterpret_cast<const int*>(c->host4 + 4) != 0) return LBM_ECUDA;
+  if (*reinterpret_cast<const int*>(c->host4 + 4) != 0) return LBM_ETIMEOUT;
   bool finite = true;
   for (int k = 0; k < 4; ++k) {
     out[k] = c->host4[k];
@@ -297,7 +306,7 @@ int lbm3_get_populations(lbm3_ctx* c, double* f, int on_device) {
   }
   LBM3_CK(cudaMemcpyAsync(c->host4 + 4, c->out4 + 4, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   LBM3_CK(cudaStreamSynchronize(c->st));
-  return *reinterpret_cast<const int*>(c->host4 + 4) != 0 ? LBM_ECUDA : LBM_OK;
+  return *reinterpret_cast<const int*>(c->host4 + 4) != 0 ? LBM_ETIMEOUT : LBM_OK;
 }
 
 int lbm3_set_populations(lbm3_ctx* c, const double* f, int on_device) {

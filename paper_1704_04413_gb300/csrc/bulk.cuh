@@ -8,6 +8,14 @@ namespace lbm {
 
 constexpr unsigned long long kBulkWaitNs = 1000000000ull;  // 1 s: a wait on a copy that never completes
 
+// Run-time control of a staged kernel's waits, passed by value.
+struct StageCtl {
+  int* status;                 // device word: set when a bounded wait gave up
+  unsigned long long wait_ns;  // limit of every bounded wait (kBulkWaitNs unless a test shortens it)
+  int fault_block;             // test hook: this block's producer announces but never issues the copies of
+                               // its last tile, so its compute warps' wait runs out; -1: off
+};
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -61,12 +69,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits until the phase of parity `parity` has completed; false after kBulkWaitNs without it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits until the phase of parity `parity` has completed; false after limit_ns without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = kBulkWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kBulkWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 

@@ -25,6 +25,7 @@ struct lbm_ctx {
   void* closure_buf = nullptr;  // features and outputs of the learned closure (lazily allocated)
   void* fd_mom = nullptr;       // rho, ux, uy, theta [4][ny][nx] of the finite-difference variant
   int* dev_err = nullptr;     // device error word (bounded device waits record LBM_ETIMEOUT there)
+  lbm::StageCtl ctl{};        // what the staged step kernels get: dev_err, wait limit, test fault hook
   long long steps = 0;
   cudaStream_t st = nullptr;
   int device = 0;

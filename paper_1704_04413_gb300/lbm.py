@@ -29,6 +29,7 @@ STORAGES = {"f64": F64, "f32": F32, "f16": F16_SHIFT, "bf16": BF16_SHIFT, "i16":
 EXPORTED = ["lbm_lattice_info", "lbm_create", "lbm_destroy", "lbm_init", "lbm_step", "lbm_moments",
             "lbm_conservation", "lbm_diagnostics", "lbm_get_populations", "lbm_set_populations",
             "lbm_step_count", "lbm_tau", "lbm_save", "lbm_load", "lbm_strerror", "lbm_last_error",
+            "lbm_test_inject_copy_fault",
             "lbm_conservation_noalloc", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_context",
             "lbm_batch_step", "lbm_batch_set_launch", "lbm_batch_get_launch", "lbm_batch_autotune",
             "lbm_closure_create", "lbm_closure_destroy", "lbm_closure_set_weights", "lbm_closure_get_weights",
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
         "lbm_get_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "lbm_set_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "lbm_step_count": (ctypes.c_longlong, [vp]),
+        "lbm_test_inject_copy_fault": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
         "lbm_tau": (ctypes.c_double, [vp]),
         "lbm_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
         "lbm_load": (ctypes.c_int, [vp, ctypes.c_char_p]),
@@ -211,6 +213,13 @@ def lbm_step_count(ctx) -> int:
     return load().lbm_step_count(ctx)
 
 
+def lbm_test_inject_copy_fault(ctx, block: int, wait_seconds: float):
+    """Testing hook of the staged step kernels' failure path (lbm.h): block >= 0 makes that block's last
+    copies never issue, so its bounded wait runs out after wait_seconds; -1 turns it off."""
+    return _check(load().lbm_test_inject_copy_fault(ctx, int(block), float(wait_seconds)), ctx,
+                  "lbm_test_inject_copy_fault")
+
+
 def lbm_tau(ctx) -> float:
     return load().lbm_tau(ctx)
 
@@ -223,13 +232,41 @@ def lbm_load(ctx, path: str):
     return _check(load().lbm_load(ctx, path.encode()), ctx, "lbm_load")
 
 
+_STORAGE_BYTES = {F64: 8, F32: 4, F16_SHIFT: 2, BF16_SHIFT: 2, I16_SHIFT: 2}
+
+
 def lbm_conservation_noalloc(lattice, storage, f, nx, ny, pitch, out4, rho0=0.0, store_scale=0.0, stream=None):
-    """Allocation-free conservation sums: f and out4 are device buffers the caller owns (torch CUDA tensors or
-    raw device addresses); the sums are written to out4 on `stream`."""
-    fp = f.data_ptr() if hasattr(f, "data_ptr") else f
-    op = out4.data_ptr() if hasattr(out4, "data_ptr") else out4
-    rc = load().lbm_conservation_noalloc(LATTICES.get(lattice, lattice), STORAGES.get(storage, storage), fp,
-                                         nx, ny, pitch, rho0, store_scale, op, stream)
+    """Allocation-free conservation sums: f and out4 are device buffers the caller owns, written on `stream`.
+
+    Torch tensors are checked before the call: both on the current CUDA device and contiguous, f with the
+    element size of `storage` and at least V * ny * pitch elements, out4 float64 with at least 4.  Raw
+    integer device addresses are passed through unchecked (the library still refuses host addresses)."""
+    lat = LATTICES.get(lattice, lattice)
+    st = STORAGES.get(storage, storage)
+    if st not in _STORAGE_BYTES:
+        raise ValueError("unknown storage %r" % (storage,))
+    if hasattr(f, "data_ptr") or hasattr(out4, "data_ptr"):
+        if not (hasattr(f, "data_ptr") and hasattr(out4, "data_ptr")):
+            raise TypeError("f and out4 must both be tensors or both be device addresses")
+        import torch
+        dev = torch.cuda.current_device()
+        for name, t in (("f", f), ("out4", out4)):
+            if not t.is_cuda or t.device.index != dev:
+                raise TypeError("%s must be a CUDA tensor on the current device (cuda:%d)" % (name, dev))
+            if not t.is_contiguous():
+                raise TypeError("%s must be contiguous" % name)
+        if f.element_size() != _STORAGE_BYTES[st]:
+            raise TypeError("f has %d-byte elements; storage %r stores %d" % (f.element_size(), storage,
+                                                                            _STORAGE_BYTES[st]))
+        V = lbm_lattice_info(lat)[0]
+        if nx < 1 or ny < 1 or pitch < nx or f.numel() < V * ny * pitch:
+            raise ValueError("f holds %d elements; V * ny * pitch = %d" % (f.numel(), V * ny * pitch))
+        if out4.dtype != torch.float64 or out4.numel() < 4:
+            raise TypeError("out4 must be a float64 tensor of at least 4 elements")
+        fp, op = f.data_ptr(), out4.data_ptr()
+    else:
+        fp, op = int(f), int(out4)
+    rc = load().lbm_conservation_noalloc(lat, st, fp, nx, ny, pitch, rho0, store_scale, op, stream)
     return _check(rc, None, "lbm_conservation_noalloc")
 
 
@@ -390,7 +427,8 @@ def lbm_closure_apply(ctx, y, u0):
 D3Q19, D3Q27, D3V39, D3Q103 = 10, 11, 12, 13
 LATTICES3 = {"D3Q19": D3Q19, "D3Q27": D3Q27, "D3V39": D3V39, "D3Q103": D3Q103}
 EXPORTED3 = ["lbm3_lattice_info", "lbm3_create", "lbm3_destroy", "lbm3_init", "lbm3_step", "lbm3_moments",
-             "lbm3_conservation", "lbm3_get_populations", "lbm3_set_populations", "lbm3_tau"]
+             "lbm3_conservation", "lbm3_get_populations", "lbm3_set_populations", "lbm3_tau",
+             "lbm3_test_inject_copy_fault"]
 
 
 class lbm3_params(ctypes.Structure):
@@ -420,6 +458,7 @@ def _l3():
             "lbm3_get_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
             "lbm3_set_populations": (ctypes.c_int, [vp, vp, ctypes.c_int]),
             "lbm3_tau": (ctypes.c_double, [vp]),
+            "lbm3_test_inject_copy_fault": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -506,3 +545,9 @@ def lbm3_set_populations(ctx, f):
 
 def lbm3_tau(ctx) -> float:
     return _l3().lbm3_tau(ctx)
+
+
+def lbm3_test_inject_copy_fault(ctx, block: int, wait_seconds: float):
+    """Testing hook of the staged 3D kernel's failure path (lbm3.h)."""
+    return _check(_l3().lbm3_test_inject_copy_fault(ctx, int(block), float(wait_seconds)),
+                  what="lbm3_test_inject_copy_fault")
