@@ -238,8 +238,8 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
   using Sc = typename Scalar<Real>::type;
   static_assert(!(THERMAL && !__is_same(Sc, Real)), "the thermal path computes one cell per thread");
   constexpr double c2 = L::CS2;
-  // highest monomial order of f the mode needs
-  constexpr int PM = (COLL == COLL_PR) ? L::NMAX : (COLL == COLL_RR ? (THERMAL ? 3 : 2) : 1);
+  // highest monomial order of f the mode needs (PR takes its orders >= 3 directly, hmom_direct below)
+  constexpr int PM = (COLL == COLL_PR) ? 2 : (COLL == COLL_RR ? (THERMAL ? 3 : 2) : 1);
   const Real rho_ref = SHIFTED ? P.rho0 : Real(1);
 
   // deviations from the reference (plain storage); shifted storage holds them already
@@ -284,6 +284,29 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
       });
     });
     if constexpr (!SHIFTED) {
+      constexpr double kp = kappa<L, Sc>(a, b);
+      if constexpr (kp != 0.0) acc += Real(kp);
+    }
+    return acc;
+  };
+
+  // Hermite moment summed directly over the populations, sum_i He_a(cx_i) He_b(cy_i) d_i (+ kappa): the
+  // projection of PR at orders >= 3.  Through the monomial moments, He_3 = c^3 - 3 cs^2 c would subtract
+  // two sums of the slow populations' large deviations (each rounded) whose difference is small; summed
+  // directly those populations enter with their small He values, which keeps the FP32 rounding of a1^(3)
+  // (amplified by He_3 / (3! cs^6) in the fast populations' rebuild) several times smaller.
+  auto hmom_direct = [&](auto Aa, auto Bb) -> Real {
+    constexpr int a = LBM_CI(Aa);
+    constexpr int b = LBM_CI(Bb);
+    Real acc = Real(0);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      constexpr double c = he(a, L::CX[i], c2) * he(b, L::CY[i], c2) * (SHIFTED ? L::W[i] : 1.0);
+      if constexpr (c != 0.0) acc = madd(Real(c), d[i], acc);
+    });
+    if constexpr (SHIFTED) {
+      acc = acc * P.inv_s;
+    } else {
       constexpr double kp = kappa<L, Sc>(a, b);
       if constexpr (kp != 0.0) acc += Real(kp);
     }
@@ -335,7 +358,11 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
         constexpr int a = LBM_CI(Aa);
         constexpr int b = n - a;
         if constexpr (L::keep(a, b)) {
-          Real v = hmom(IC<a>{}, IC<b>{});
+          Real v;
+          if constexpr (n <= 2)
+            v = hmom(IC<a>{}, IC<b>{});
+          else
+            v = hmom_direct(IC<a>{}, IC<b>{});
           if (n <= P.neq) v -= A[a][b];
           B[a][b] = v;
         }

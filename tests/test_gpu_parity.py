@@ -1,9 +1,16 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
 
 Tolerances: FP32 compute and storage within 1e-6 per population for one
-collision, relative to max(|f_i|, w_i) (gpu_util.pop_rel) and within 1e-4 relative L2 on rho and u after 500 steps of the
-64x64 shear layer; FP64 compute and storage within 1e-12 (per collision) and
-1e-10 relative L2 after 500 steps.
+collision of the stored populations, relative to max(|f_i|, w_i) on every
+population and relative to |f_i| itself on every population with
+|f_i| >= w_i / 10 (gpu_util.assert_coll; 2e-6 for D2V17 PR, tol_big),
+and within 1e-4 relative L2 on rho and u after 500 steps of the 64x64 shear
+layer; FP64 compute and storage within 1e-12 (per collision) and 1e-10
+relative L2 after 500 steps.
+
+Grids of 5 or 6 rows run every row through the kernels' general (edge) load
+path on the wide lattices (D2V17, D2V37 reach 3 rows); grids of 16 rows also
+run their interior rows through the single interior load sequence.
 """
 import os
 import tempfile
@@ -14,7 +21,7 @@ import pytest
 from oracle import oracle as orc
 from paper_1704_04413_gb300 import workloads as wl
 
-from gpu_util import Ctx, lib, max_rel, perm, pop_rel, rel_l2
+from gpu_util import Ctx, assert_coll, lib, max_rel, perm, pop_rel, rel_l2, stored
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +40,17 @@ MODES = [
 ]
 
 
+def tol_big(name, coll, storage):
+    """Plain relative bound on populations with |f_i| >= w_i / 10.  PR at order 3 on D2V17 in FP32 rebuilds
+    its (2, 2)-type populations, which the collision drives to 0.1-0.2 w_i, from terms of order w_i with
+    third-order Hermite factors up to 5.8: FP32 rounding of the rebuild alone (the kernel's operation order
+    emulated with round-to-nearest FP32 in numpy) reaches 1.4e-6 relative on them, 5.5e-7 with that rebuild
+    in FP64.  Its bound is 2e-6; every other mode, and the same populations relative to w_i, keep 1e-6."""
+    if name == "D2V17" and coll == "pr" and storage == "f32":
+        return 2e-6
+    return TOL_COLL[storage]
+
+
 def oracle_state(name, nx, ny, seed, thermal, eps=0.02, neq=None):
     """Oracle-initialised non-equilibrium populations: f^(0) of smooth random fields times (1 + eta)."""
     L = orc.lattice(name)
@@ -42,56 +60,59 @@ def oracle_state(name, nx, ny, seed, thermal, eps=0.02, neq=None):
     return f * (1.0 + wl.population_noise(L.V, nx, ny, seed + 1, eps))
 
 
+@pytest.mark.parametrize("ny", [5, 16])
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 @pytest.mark.parametrize("name,coll,neq,nreg,thermal", MODES)
-def test_one_step_matches_oracle(name, coll, neq, nreg, thermal, storage):
-    nx, ny, tau = 300, 5, 0.62  # 300 = two 128-wide tiles and a ragged tail
+def test_one_step_matches_oracle(name, coll, neq, nreg, thermal, storage, ny):
+    nx, tau = 300, 0.62  # 300 = two 128-wide tiles and a ragged tail
     f = oracle_state(name, nx, ny, 11, thermal)
     op = orc.params(name, nx, ny, tau, coll, neq, nreg, thermal=thermal)
-    ref = orc.step(op, f)
+    ref = orc.step(op, stored(f, storage))
     with Ctx(name, nx, ny, tau, coll, neq, nreg, storage, thermal) as c:
         c.set_oracle_f(f)
         c.step(1)
         got = c.get_oracle_f()
-    assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
+    assert_coll(got, ref, orc.lattice(name).w, TOL_COLL[storage], tol_big(name, coll, storage))
 
 
 PER_ORDER = [m for m in MODES if m[1] != "bgk" and (m[3] == 0 or m[3] >= 3)]
 
 
+@pytest.mark.parametrize("ny", [5, 16])
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 @pytest.mark.parametrize("name,coll,neq,nreg,thermal", PER_ORDER)
-def test_one_step_with_per_order_times_matches_oracle(name, coll, neq, nreg, thermal, storage):
+def test_one_step_with_per_order_times_matches_oracle(name, coll, neq, nreg, thermal, storage, ny):
     """Eq. GenRegCollision with one relaxation time per order of f^(1): tau_2 = 0.62, tau_3 = 0.55,
     tau_4 = 1.3 (order 4 only where the lattice keeps it)."""
-    nx, ny, tau, tau3, tau4 = 300, 5, 0.62, 0.55, 1.3
+    nx, tau, tau3, tau4 = 300, 0.62, 0.55, 1.3
     f = oracle_state(name, nx, ny, 17, thermal)
     op = orc.params(name, nx, ny, tau, coll, neq, nreg, thermal=thermal, tau3=tau3, tau4=tau4)
-    ref = orc.step(op, f)
+    ref = orc.step(op, stored(f, storage))
     with Ctx(name, nx, ny, tau, coll, neq, nreg, storage, thermal, tau3=tau3, tau4=tau4) as c:
         c.set_oracle_f(f)
         c.step(1)
         got = c.get_oracle_f()
-    assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
+    assert_coll(got, ref, orc.lattice(name).w, TOL_COLL[storage], tol_big(name, coll, storage))
 
 
 FD_MODES = [m for m in MODES if m[1] == "rr"]
 
 
+@pytest.mark.parametrize("ny", [5, 16])
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 @pytest.mark.parametrize("name,coll,neq,nreg,thermal", FD_MODES)
-def test_one_step_with_finite_difference_a1_matches_oracle(name, coll, neq, nreg, thermal, storage):
+def test_one_step_with_finite_difference_a1_matches_oracle(name, coll, neq, nreg, thermal, storage, ny):
     """RR with a1^(2) (and the thermal temperature-gradient terms) from central differences of the
-    post-streaming fields (Sec. II.E), one step on a ragged 300 x 5 grid, tau_3 != tau."""
-    nx, ny, tau = 300, 5, 0.62
+    post-streaming fields (Sec. II.E), one step on a ragged 300 x ny grid, tau_3 != tau."""
+    nx, tau = 300, 0.62
     f = oracle_state(name, nx, ny, 19, thermal)
     op = orc.params(name, nx, ny, tau, coll, neq, nreg, thermal=thermal, tau3=0.7, a1_source=1)
-    ref = orc.step(op, f)
+    ref = orc.step(op, stored(f, storage))
     with Ctx(name, nx, ny, tau, coll, neq, nreg, storage, thermal, tau3=0.7, a1_source=1) as c:
         c.set_oracle_f(f)
         c.step(1)
         got = c.get_oracle_f()
-    assert pop_rel(got, ref, orc.lattice(name).w) <= TOL_COLL[storage]
+    assert_coll(got, ref, orc.lattice(name).w, TOL_COLL[storage])
 
 
 @pytest.mark.parametrize("name,thermal,storage", [("D2Q9", False, "f64"), ("D2V37", True, "f64"),
@@ -159,7 +180,7 @@ def test_init_and_moments_match_oracle(name, neq, thermal, storage):
         mom = c.moments()
         cons = c.m.lbm_conservation(c.ctx)
     tol = TOL_COLL[storage]
-    assert pop_rel(got, ref, orc.lattice(name).w) <= tol
+    assert_coll(got, ref, orc.lattice(name).w, tol)
     for a, b in zip(mom, mref):
         assert np.max(np.abs(a - b)) <= 10 * tol * max(1.0, np.max(np.abs(b)))
     cref = orc.conservation(op, ref)
@@ -205,12 +226,13 @@ def test_diagnostics_match_oracle():
     assert np.max(np.abs(d - d_o) / np.abs(d_o)) <= 1e-9
 
 
+@pytest.mark.parametrize("ny", [6, 16])
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
 @pytest.mark.parametrize("name,thermal", [("D2Q9", False), ("D2V17", False), ("D2V37", False), ("D2V37", True)])
-def test_shifted_low_precision_storage(name, thermal, storage, tol):
+def test_shifted_low_precision_storage(name, thermal, storage, tol, ny):
     """Shifted FP16/BF16 storage g = (f/w - rho0) s: one step against the oracle, error relative to
     the deviation scale max|f/w - rho0| (what the format resolves)."""
-    nx, ny, tau = 150, 6, 0.7
+    nx, tau = 150, 0.7
     f = oracle_state(name, nx, ny, 8, thermal)
     Lt = orc.lattice(name)
     op = orc.params(name, nx, ny, tau, "rr", Lt.nmax, thermal=thermal)
@@ -284,27 +306,36 @@ def test_mass_and_momentum_conserved_over_steps():
     assert np.max(np.abs(c1[1:3] - c0[1:3])) <= 1e-12 * abs(c0[0])
 
 
-def test_full_size_sampled_parity_d2v37():
-    """1024x1024 D2V37 RR FP32, the benchmark's largest shear-layer grid and launch shape: one step from the
-    oracle's initial state (f^(0) + f^(1)), 2000 sampled cells (including edges and corners) checked
-    cell by cell against the oracle."""
-    name, L = "D2V37", 1024
+@pytest.mark.parametrize("name,storage,tol", [("D2Q9", "f32", None), ("D2V17", "f32", None), ("D2V37", "f32", None),
+                                              ("D2Q9", "f16", 2e-3), ("D2V17", "f16", 2e-3), ("D2V17", "bf16", 2e-2)])
+def test_full_size_sampled_parity(name, storage, tol):
+    """1024 x 1024 RR shear layer at the benchmark's equilibrium orders (D2Q9 N = 2, D2V17 N = 3, D2V37
+    N = 4) and launch shapes: one step from the oracle's initial state (f^(0) + f^(1)), 2000 sampled
+    cells (interior, edges and corners) checked cell by cell against the oracle.  FP32 at the
+    per-collision bound; 16-bit storage (the staged pair kernel on D2Q9 / D2V17) relative to the
+    deviation scale the format resolves."""
+    L = 1024
+    neq = {"D2Q9": 2, "D2V17": 3, "D2V37": 4}[name]
     Lt = orc.lattice(name)
     u0, nu, _ = wl.shear_layer_params(L, np.sqrt(Lt.cs2), 0.1, 3e4)
     fl = wl.double_shear_layer(L, u0)
     tau = orc.tau_from_nu(Lt.cs2, nu)
-    op = orc.params(name, L, L, tau, "rr", 4)
+    op = orc.params(name, L, L, tau, "rr", neq)
     f = orc.init(op, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
     rng = np.random.default_rng(0)
     cells = np.concatenate([rng.integers(0, L * L, 1900), np.arange(0, L, 11), np.arange(0, L * L, L * 37)[:30],
                             [L - 1, L * L - 1, L * (L - 1)]])
-    with Ctx(name, L, L, tau, "rr", 4, 0, "f32") as c:
+    with Ctx(name, L, L, tau, "rr", neq, 0, storage) as c:
         c.set_oracle_f(f)
         c.step(1)
         got = c.get_oracle_f()
-    ref = orc.step_cells(op, f, cells)
+    ref = orc.step_cells(op, stored(f, storage), cells).T
     got_s = got.reshape(Lt.V, -1)[:, cells]
-    assert pop_rel(got_s, ref.T, Lt.w) <= 1e-6
+    if storage == "f32":
+        assert_coll(got_s, ref, Lt.w, 1e-6)
+    else:
+        w = Lt.w[:, None]
+        assert np.max(np.abs(got_s - ref) / w) <= tol * np.abs(ref / w - 1.0).max()
 
 
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
@@ -332,20 +363,22 @@ def test_large_grid_16bit_d2v37_sampled_parity(storage, tol):
     assert np.max(np.abs(got - ref) / w) <= tol * dev
 
 
+@pytest.mark.parametrize("ny", [6, 16])
 @pytest.mark.parametrize("bcy", [0, 1])
 @pytest.mark.parametrize("nx", [64, 1040])
 @pytest.mark.parametrize("storage,tol", [("f32", None), ("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
 @pytest.mark.parametrize("name", ["D2Q9", "D2V17"])
-def test_staged_pair_tiles(name, storage, tol, nx, bcy):
+def test_staged_pair_tiles(name, storage, tol, nx, bcy, ny):
     """With binary16 or bfloat16 storage, x-periodic grids with whole 16-byte rows take the staged pair
     kernel: nx = 64 is one tile (the row staged whole, wrapped by index), nx = 1040 two 512-cell tiles and a
     ragged one whose edge tiles copy the wrapped columns; a zero-gradient y edge clamps the staged source
-    rows.  FP32 and fixed point run the same cases through the direct pair kernel.  Three RR steps."""
-    ny, tau, steps = 6, 0.62, 3
+    rows.  FP32 and fixed point run the same cases through the direct pair kernel.  Three RR steps; with 16
+    rows the direct pair kernel's interior rows take its single interior load sequence."""
+    tau, steps = 0.62, 3
     Lt = orc.lattice(name)
     f = oracle_state(name, nx, ny, 21, False, neq=Lt.nmax)
     op = orc.params(name, nx, ny, tau, "rr", Lt.nmax, bc_x=0, bc_y=bcy)
-    ref = orc.step(op, f, steps)
+    ref = orc.step(op, stored(f, storage), steps)
     with Ctx(name, nx, ny, tau, "rr", Lt.nmax, 0, storage, False, bcx=0, bcy=bcy) as c:
         c.set_oracle_f(f)
         c.step(steps)
