@@ -1,16 +1,17 @@
 // Batched stream-and-collide: many independent grids (D2Q9 and D2V17, uneven
-// sizes and relaxation times) advanced by one launch per lattice per time step
-// (a single launch when all instances share a lattice), the launches captured
-// in a CUDA graph.
+// sizes and relaxation times) advanced by one kernel launch per time step, the
+// launches captured in a CUDA graph (one kernel node per step).
 //
 // Work item = `rows` consecutive rows x (2 * threads) columns of one
-// instance; items of all instances of a lattice are numbered consecutively and
+// instance; the items of all instances are numbered consecutively, those of
+// the D2V17 instances (twice the bytes and arithmetic per cell) first, and
 // either one block per item or a persistent grid of (SMs x blocks per SM)
-// blocks walks them.  The instance table travels
-// as a kernel parameter (constant bank); each item finds its instance by a
-// binary search over the first-item offsets.  Per cell the arithmetic is the
-// single-grid two-cell kernel's (step2_cells), so a batched step is bitwise
-// identical to per-instance lbm_step calls.
+// blocks walks them.  The instance table travels as a kernel parameter
+// (constant bank); each item finds its instance by a binary search over the
+// first-item offsets and takes that instance's lattice (a block-uniform
+// branch).  Per cell the arithmetic is the single-grid two-cell kernel's
+// (step2_cells), so a batched step is bitwise identical to per-instance
+// lbm_step calls.
 //
 // The launch shape (threads per block, rows per item, blocks per SM) is chosen
 // by lbm_batch_autotune, which times every candidate on the batch itself.
@@ -34,6 +35,7 @@ struct BatchInst {
   StepGeom g;
   CollParams<F2> P;
   int ntx;         // items per row band
+  int lattice;     // LBM_D2Q9 or LBM_D2V17
   long long item0; // first work item of the instance
 };
 
@@ -44,7 +46,20 @@ struct BatchDesc {
   BatchInst inst[kBatchMax];
 };
 
+// The rows of one work item of instance I on lattice L.
 template <class L, int COLL, class S>
+__device__ __forceinline__ void batch_item(const BatchInst& I, int rows, int band, int x, int xw) {
+  const S* fin = static_cast<const S*>(I.fin);
+  S* fout = static_cast<S*>(I.fout);
+  const GeomOffsets<L, S> off{I.g.plane * (long long)sizeof(S), (long long)I.g.pitch * (long long)sizeof(S)};
+  for (int r = 0; r < rows; ++r) {
+    const int y = band * rows + r;
+    if (y >= I.g.ny) break;
+    step2_cells<L, COLL, S>(fin, fout, I.g, I.P, off, x, y, xw);
+  }
+}
+
+template <int COLL, class S>
 __global__ void __launch_bounds__(256, 1) k_batch(const __grid_constant__ BatchDesc d) {
   for (long long it = blockIdx.x; it < d.total; it += gridDim.x) {
     int lo = 0, hi = d.n - 1;
@@ -59,45 +74,40 @@ __global__ void __launch_bounds__(256, 1) k_batch(const __grid_constant__ BatchD
     const int x = 2 * (tx * (int)blockDim.x + (int)threadIdx.x);
     const int xw = 2 * (tx * (int)blockDim.x + (int)(threadIdx.x & ~31u));
     if (x >= I.g.nx) continue;
-    const S* fin = static_cast<const S*>(I.fin);
-    S* fout = static_cast<S*>(I.fout);
-    for (int r = 0; r < d.rows; ++r) {
-      const int y = band * d.rows + r;
-      if (y >= I.g.ny) break;
-      GeomOffsets<L, S> off{I.g.plane * (long long)sizeof(S), (long long)I.g.pitch * (long long)sizeof(S)};
-      step2_cells<L, COLL, S>(fin, fout, I.g, I.P, off, x, y, xw);
-    }
+    if (I.lattice == LBM_D2V17)
+      batch_item<D2V17, COLL, S>(I, d.rows, band, x, xw);
+    else
+      batch_item<D2Q9, COLL, S>(I, d.rows, band, x, xw);
   }
 }
 
 // blocks_per_sm == 0: one block per work item; > 0: persistent grid of blocks_per_sm x SMs blocks.
-template <class L, int COLL, class S>
+template <int COLL, class S>
 cudaError_t batch_launch_t(const BatchDesc& d, int threads, int blocks_per_sm, int nsm, cudaStream_t st) {
   if (d.n == 0 || d.total == 0) return cudaSuccess;
   long long grid = blocks_per_sm > 0 ? (long long)blocks_per_sm * nsm : d.total;
   if (grid > d.total) grid = d.total;
   if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
-  k_batch<L, COLL, S><<<(unsigned)grid, threads, 0, st>>>(d);
+  k_batch<COLL, S><<<(unsigned)grid, threads, 0, st>>>(d);
   return cudaGetLastError();
 }
 
-template <class L, class S>
+template <class S>
 cudaError_t batch_launch_s(int coll, const BatchDesc& d, int threads, int bps, int nsm, cudaStream_t st) {
   switch (coll) {
-    case COLL_BGK: return batch_launch_t<L, COLL_BGK, S>(d, threads, bps, nsm, st);
-    case COLL_PR: return batch_launch_t<L, COLL_PR, S>(d, threads, bps, nsm, st);
-    case COLL_RR: return batch_launch_t<L, COLL_RR, S>(d, threads, bps, nsm, st);
+    case COLL_BGK: return batch_launch_t<COLL_BGK, S>(d, threads, bps, nsm, st);
+    case COLL_PR: return batch_launch_t<COLL_PR, S>(d, threads, bps, nsm, st);
+    case COLL_RR: return batch_launch_t<COLL_RR, S>(d, threads, bps, nsm, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <class L>
-cudaError_t batch_launch_l(int coll, int prec, const BatchDesc& d, int threads, int bps, int nsm, cudaStream_t st) {
+cudaError_t batch_launch(int coll, int prec, const BatchDesc& d, int threads, int bps, int nsm, cudaStream_t st) {
   switch (prec) {
-    case PREC_F32: return batch_launch_s<L, float>(coll, d, threads, bps, nsm, st);
-    case PREC_F16: return batch_launch_s<L, __half>(coll, d, threads, bps, nsm, st);
-    case PREC_BF16: return batch_launch_s<L, __nv_bfloat16>(coll, d, threads, bps, nsm, st);
-    case PREC_I16: return batch_launch_s<L, short>(coll, d, threads, bps, nsm, st);
+    case PREC_F32: return batch_launch_s<float>(coll, d, threads, bps, nsm, st);
+    case PREC_F16: return batch_launch_s<__half>(coll, d, threads, bps, nsm, st);
+    case PREC_BF16: return batch_launch_s<__nv_bfloat16>(coll, d, threads, bps, nsm, st);
+    case PREC_I16: return batch_launch_s<short>(coll, d, threads, bps, nsm, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -120,36 +130,34 @@ struct lbm_batch {
 
 namespace {
 
-// Launch descriptor of the instances of one lattice, each reading buffer cur ^ flip.
-BatchDesc make_desc(const lbm_batch* b, int lattice, int flip) {
+// Launch descriptor of every instance, each reading buffer cur ^ flip: the D2V17 instances' items first.
+BatchDesc make_desc(const lbm_batch* b, int flip) {
   BatchDesc d{};
   d.n = 0;
   d.rows = b->rows;
   long long item = 0;
-  for (int k = 0; k < b->n; ++k) {
-    const lbm_ctx* c = b->ctx[k];
-    if (c->p.lattice != lattice) continue;
-    BatchInst& I = d.inst[d.n++];
-    const int cur = c->cur ^ flip;
-    I.fin = c->buf[cur];
-    I.fout = c->buf[cur ^ 1];
-    I.g = c->g;
-    I.P = cast_params<F2>(lbm_ctx_coll_params(c));
-    I.ntx = (c->p.nx + 2 * b->threads - 1) / (2 * b->threads);
-    I.item0 = item;
-    item += (long long)I.ntx * ((c->p.ny + b->rows - 1) / b->rows);
-  }
+  for (int lattice : {LBM_D2V17, LBM_D2Q9})
+    for (int k = 0; k < b->n; ++k) {
+      const lbm_ctx* c = b->ctx[k];
+      if (c->p.lattice != lattice) continue;
+      BatchInst& I = d.inst[d.n++];
+      const int cur = c->cur ^ flip;
+      I.fin = c->buf[cur];
+      I.fout = c->buf[cur ^ 1];
+      I.g = c->g;
+      I.P = cast_params<F2>(lbm_ctx_coll_params(c));
+      I.ntx = (c->p.nx + 2 * b->threads - 1) / (2 * b->threads);
+      I.lattice = lattice;
+      I.item0 = item;
+      item += (long long)I.ntx * ((c->p.ny + b->rows - 1) / b->rows);
+    }
   d.total = item;
   return d;
 }
 
-// One batched time step: a launch per lattice present.
+// One batched time step: one launch over the instances of both lattices.
 cudaError_t batch_step_launch(const lbm_batch* b, int flip, cudaStream_t st) {
-  cudaError_t e = batch_launch_l<D2Q9>(b->coll, b->prec, make_desc(b, LBM_D2Q9, flip), b->threads, b->blocks_per_sm,
-                                       b->nsm, st);
-  if (e != cudaSuccess) return e;
-  return batch_launch_l<D2V17>(b->coll, b->prec, make_desc(b, LBM_D2V17, flip), b->threads, b->blocks_per_sm, b->nsm,
-                               st);
+  return batch_launch(b->coll, b->prec, make_desc(b, flip), b->threads, b->blocks_per_sm, b->nsm, st);
 }
 
 void drop_graphs(lbm_batch* b) {
