@@ -33,7 +33,7 @@ class _Group:
     """Independent shear-layer instances stepped together: a batch where the lattice allows, else a list of
     contexts advanced one after the other on the same stream."""
 
-    def __init__(self, lattice, collision, reg_order, L, machs_res, storage, stream):
+    def __init__(self, lattice, collision, reg_order, L, machs_res, storage, stream, a1_source=0):
         V, cx, cy, w, cs2 = lbm.lbm_lattice_info(lattice)
         self.cs = math.sqrt(cs2)
         self.params, fields = [], []
@@ -42,10 +42,10 @@ class _Group:
             nu = u0 * L / re
             self.params.append(lbm.make_params(lattice, L, L, nu=nu, collision=collision,
                                                hermite_order=MAX_ORDER[lattice], reg_order=reg_order,
-                                               storage=storage, stream=stream))
+                                               storage=storage, stream=stream, a1_source=a1_source))
             fields.append(wl.double_shear_layer(L, u0))
         self.batch = None
-        if lattice in ("D2Q9", "D2V17") and storage != "f64":
+        if lattice in ("D2Q9", "D2V17") and storage != "f64" and a1_source == 0:
             self.batch = lbm.lbm_batch_create(self.params)
             self.ctxs = [lbm.lbm_batch_context(self.batch, i) for i in range(len(self.params))]
         else:
@@ -73,9 +73,10 @@ def _mean_u2(ctx):
     return float(d[0]) if np.isfinite(d).all() else math.inf
 
 
-def run_group(lattice, collision, reg_order, L, machs_res, storage="f32", check=20, stream=None):
-    """Stability verdicts of instances (M0, Re): True when <u^2> stays below its initial value up to 2 t_c."""
-    g = _Group(lattice, collision, reg_order, L, machs_res, storage, stream)
+def run_group(lattice, collision, reg_order, L, machs_res, storage="f32", check=20, stream=None, a1_source=0):
+    """Stability verdicts of instances (M0, Re): True when <u^2> stays below its initial value up to 2 t_c.
+    a1_source = 1: RR with a1 from finite differences of the fields (Sec. II.E) instead of the projection."""
+    g = _Group(lattice, collision, reg_order, L, machs_res, storage, stream, a1_source)
     try:
         ends = [steps_to(L, m, g.cs) for m, _ in machs_res]
         e0 = [_mean_u2(c) for c in g.ctxs]
@@ -99,7 +100,7 @@ def run_group(lattice, collision, reg_order, L, machs_res, storage="f32", check=
 
 
 def max_mach(lattice, collision, reynolds, reg_order=0, L=128, lo=0.0, hi=1.5, dm=0.01, points=None,
-             storage="f32", check=20, stream=None, max_instances=64):
+             storage="f32", check=20, stream=None, max_instances=64, a1_source=0):
     """M0^max per Reynolds number: dict Re -> (largest stable M0 below the smallest unstable one, smallest
     unstable M0), to dm.  0.0 as the first value means no tested Mach number was stable; None as the second
     means every tested one was."""
@@ -126,7 +127,9 @@ def max_mach(lattice, collision, reynolds, reg_order=0, L=128, lo=0.0, hi=1.5, d
             break
         for k in range(0, len(jobs), max_instances):
             chunk = jobs[k:k + max_instances]
-            for (m, re), ok in zip(chunk, run_group(lattice, collision, reg_order, L, chunk, storage, check, stream)):
+            verdicts = run_group(lattice, collision, reg_order, L, chunk, storage, check, stream, a1_source) \
+                if a1_source else run_group(lattice, collision, reg_order, L, chunk, storage, check, stream)
+            for (m, re), ok in zip(chunk, verdicts):
                 tried[re][m] = ok
     out = {}
     for re in reynolds:
@@ -135,30 +138,35 @@ def max_mach(lattice, collision, reynolds, reg_order=0, L=128, lo=0.0, hi=1.5, d
     return out
 
 
-def stability_map(reynolds=(1e4, 1e5, 1e6), L=128, lattices=("D2Q9", "D2V17", "D2V37"), storage="f32", check=20,
+def stability_map(reynolds=(1e4, 3e4, 1e5, 1e6), L=128, lattices=("D2Q9", "D2V17", "D2V37"), storage="f32", check=20,
                   stream=None, variants=None):
     """M0^max per lattice, collision variant and Reynolds number.  Variants (default all): "bgk", "pr<N>" for
     the projection at every order N from 2 to the lattice maximum (PR-2 is the standard second-order
     projection; PR at the maximal order is the projection onto the lattice's whole Hermite basis, BGK
     itself on the complete D2Q9 basis) and "rr<N>" for the recursive regularization at every order from 3
-    to the maximum ("rr2" would repeat "pr2").  "pr_best" / "rr_best" are the most stable order of each."""
+    to the maximum ("rr2" would repeat "pr2"); "rrfd<N>" is RR-N with a1 from finite differences of the
+    fields instead of the projection (Sec. II.E allows both).  "pr_best", "rr_projection_best" and
+    "rr_fd_best" are the most stable order of each family, "rr_best" the most stable RR of either kind."""
     out = {}
     for lat in lattices:
         t0 = time.perf_counter()
         nmax = MAX_ORDER[lat]
         names = variants or (["bgk"] + ["pr%d" % n for n in range(2, nmax + 1)] +
-                             ["rr%d" % n for n in range(3, nmax + 1)])
+                             ["rr%d" % n for n in range(3, nmax + 1)] + ["rrfd%d" % n for n in range(3, nmax + 1)])
         res = {}
         for v in names:
-            coll, order = (v, 0) if v == "bgk" else (v[:2], int(v[2:]))
+            fd = v.startswith("rrfd")
+            coll, order = (v, 0) if v == "bgk" else (v[:2], int(v[4:] if fd else v[2:]))
             if order > nmax:
                 continue
             res[v] = max_mach(lat, coll, reynolds, reg_order=order, L=L, storage=storage, check=check,
-                              stream=stream)
-        for fam in ("pr", "rr"):
-            keys = [k for k in res if k.startswith(fam)]
+                              stream=stream, a1_source=1 if fd else 0)
+        for fam, keys in (("pr_best", [k for k in res if k.startswith("pr")]),
+                          ("rr_projection_best", [k for k in res if k.startswith("rr") and not k.startswith("rrfd")]),
+                          ("rr_fd_best", [k for k in res if k.startswith("rrfd")]),
+                          ("rr_best", [k for k in res if k.startswith("rr")])):
             if keys:
-                res[fam + "_best"] = {re: max(res[k][re][0] for k in keys) for re in reynolds}
+                res[fam] = {re: max(res[k][re][0] for k in keys) for re in reynolds}
         res["seconds"] = round(time.perf_counter() - t0, 2)
         out[lat] = res
     return out
