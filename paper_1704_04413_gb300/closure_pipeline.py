@@ -20,13 +20,14 @@ from . import workloads as wl
 class ClosureData:
     x: object            # [N, 32] BF16 features (CUDA tensor)
     y: object            # [N, 8] FP32 targets (CUDA tensor)
-    truth: dict          # coarse-step index -> filtered (rho, ux, uy) of the evaluation seed (host)
+    truth: dict          # coarse-step index -> filtered (rho, ux, uy) of the first training seed (host)
     u0: float
     nu_coarse: float
     coarse: int
     factor: int
     fine_finite: list = field(default_factory=list)
     seconds: float = 0.0
+    held_out: dict = field(default_factory=dict)  # seed -> truth dict of fine runs kept out of training
 
 
 def _vorticity(u, v):
@@ -52,8 +53,9 @@ def spectrum_error(u, v, u_ref, v_ref):
 
 
 def generate(fine: int, factor: int, reynolds: float, seeds, convective_times: float = 1.0, snapshots: int = 16,
-             mach: float = 0.1, stream=None) -> ClosureData:
-    """Fine D2Q9 RR shear layers (seeded kappa, delta), box-filtered by `factor` every few coarse steps."""
+             mach: float = 0.1, stream=None, held_out=()) -> ClosureData:
+    """Fine D2Q9 RR shear layers (seeded kappa, delta), box-filtered by `factor` every few coarse steps.
+    The runs of `seeds` give the training samples; those of `held_out` give only evaluation truths."""
     import torch
     st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     t0 = time.perf_counter()
@@ -64,8 +66,10 @@ def generate(fine: int, factor: int, reynolds: float, seeds, convective_times: f
     total = int(round(convective_times * steps_tc)) // factor * factor
     every = max(factor, (total // snapshots) // factor * factor)
     dev = lambda n: torch.zeros((n, n), dtype=torch.float64, device="cuda")
-    X, Y, truth, finite = [], [], {}, []
-    for k, seed in enumerate(seeds):
+    X, Y, truth, finite, held = [], [], {}, [], {}
+    seeds = list(seeds)
+    for k, seed in enumerate(seeds + list(held_out)):
+        train = k < len(seeds)
         fl = wl.perturbed_shear_layer(fine, u0, seed)
         ctx = lbm.lbm_create(lbm.make_params("D2Q9", fine, fine, nu=nu_f, collision="rr", hermite_order=2,
                                              storage="f32", stream=st))
@@ -81,15 +85,20 @@ def generate(fine: int, factor: int, reynolds: float, seeds, convective_times: f
                 lbm.lbm_closure_coarsen(rho, ux, uy, fine, fine, factor, u0, rc, uc, vc, y, st)
                 x = torch.zeros((coarse * coarse, lbm.CLOSURE_IN), dtype=torch.bfloat16, device="cuda")
                 lbm.lbm_closure_features(rc, uc, vc, coarse, coarse, u0, x, st)
-                X.append(x)
-                Y.append(y)
+                if train:
+                    X.append(x)
+                    Y.append(y)
+                fields = (rc.cpu().numpy(), uc.cpu().numpy(), vc.cpu().numpy())
                 if k == 0:
-                    truth[s // factor] = (rc.cpu().numpy(), uc.cpu().numpy(), vc.cpu().numpy())
+                    truth[s // factor] = fields
+                if not train:
+                    held.setdefault(seed, {})[s // factor] = fields
             finite.append(bool(torch.isfinite(rho).all().item()))
         finally:
             lbm.lbm_destroy(ctx)
     torch.cuda.synchronize()
-    return ClosureData(torch.cat(X), torch.cat(Y), truth, u0, nu_c, coarse, factor, finite, time.perf_counter() - t0)
+    return ClosureData(torch.cat(X), torch.cat(Y), truth, u0, nu_c, coarse, factor, finite, time.perf_counter() - t0,
+                       held)
 
 
 def train(data: ClosureData, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
@@ -116,13 +125,15 @@ def train(data: ClosureData, epochs: int = 20, batch: int = 4096, lr: float = 1e
     return cl, losses, time.perf_counter() - t0
 
 
-def compare(data: ClosureData, cl, stream=None):
+def compare(data: ClosureData, cl, stream=None, truth=None):
     """Coarse runs from the filtered initial state: plain RR and RR with the closure, each snapshot's
-    vorticity-spectrum error and vorticity relative L2 error against the filtered fine run."""
+    vorticity-spectrum error and vorticity relative L2 error against the filtered fine run (`truth`, default
+    the first training seed's)."""
     import torch
     st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     n = data.coarse
-    r0, u0f, v0f = data.truth[0]
+    truth = truth if truth is not None else data.truth
+    r0, u0f, v0f = truth[0]
     gx = lambda a: (np.roll(a, -1, 1) - np.roll(a, 1, 1)) / 2.0
     gy = lambda a: (np.roll(a, -1, 0) - np.roll(a, 1, 0)) / 2.0
     grad = np.ascontiguousarray(np.stack([gx(u0f), gy(u0f), gx(v0f), gy(v0f)]))
@@ -133,7 +144,7 @@ def compare(data: ClosureData, cl, stream=None):
         try:
             lbm.lbm_init(c, np.ascontiguousarray(r0), np.ascontiguousarray(u0f), np.ascontiguousarray(v0f), None, grad)
             done, rows = 0, []
-            for s in sorted(data.truth)[1:]:
+            for s in sorted(truth)[1:]:
                 if mode == "plain":
                     lbm.lbm_step(c, s - done)
                 else:
@@ -141,7 +152,7 @@ def compare(data: ClosureData, cl, stream=None):
                 done = s
                 rr, uu, vv = (np.empty((n, n)) for _ in range(3))
                 lbm.lbm_moments(c, rr, uu, vv)
-                _, ut, vt = data.truth[s]
+                _, ut, vt = truth[s]
                 wt, wc = _vorticity(ut, vt), _vorticity(uu, vv)
                 rows.append({"coarse_step": s, "spectrum_err": spectrum_error(uu, vv, ut, vt),
                              "vorticity_rel_l2": float(np.linalg.norm(wc - wt) / np.linalg.norm(wt))})
