@@ -2,11 +2,13 @@
 """Throughput of the RR stream-and-collide step on GB300 (one JSON line on stdout).
 
 Workload: the doubly periodic shear layer of Sec. III.B at Re = 3e4, Ma = 0.1,
-on 1024^2 grids, one context per lattice: D2Q9 (2nd-order equilibrium),
-D2V17 (3rd order) and D2V37 (4th order), RR collision, FP32 compute and FP32
-storage.  One bench step = one lbm_step on each of the three lattices.
+on 1024^2 grids, one grid per lattice: D2Q9 (2nd-order equilibrium), D2V17
+(3rd order) and D2V37 (4th order), RR collision, FP32 compute and FP32
+storage.  One bench step advances all three grids by one time step, as one
+batch (lbm_batch_step: a single kernel launch per step, graph-replayed).
 `value` is the aggregate GLUPS (cells updated per second, all lattices, all
-ranks); per-lattice GLUPS, HBM roofline fractions and the low-precision
+ranks); per-lattice GLUPS (each grid stepped by its own context), HBM
+roofline fractions and the low-precision
 (shifted FP16 / BF16) and FP64 variants are reported alongside, with further
 sections (4096^2 grids, finite-difference a1, accuracy, batched sweep, learned
 closure, stability map, and the 3D lattices of Tab. II on a 256^3 Taylor-Green
@@ -46,25 +48,26 @@ HEADLINE_ORDER = ("D2V17", "D2Q9", "D2V37")
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2, "i16": 2}
 METRIC = "RR stream-collide GLUPS & HBM-roofline fraction per lattice; low-prec vs FP32"
 REF_BAND = 128  # rows of the oracle's sample band
-PROFILE = os.path.join(ROOT, "profiles", "step_d2v37_rr_f32_1024.txt")
+PROFILE = os.path.join(ROOT, "profiles", "batch_rr_f32_3x1024.txt")
+PROFILE_SOURCES = ("lattice.cuh", "collide.cuh", "step.cuh", "vec2.cuh", "batch.cu")
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=PROFILE_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1704_04413_gb300", "csrc")
-    for fn in ("lattice.cuh", "collide.cuh", "step.cuh", "step_d2v37.cu"):
+    for fn in files:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """dram bytes per launch of the D2V37 RR FP32 kernel from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(path=PROFILE):
+    """dram bytes per launch of the timed kernel (the batched three-lattice step) from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    if not os.path.exists(path):
         return None
     vals = {}
-    for line in open(PROFILE):
+    for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
@@ -163,6 +166,44 @@ def make_contexts(storage, stream, grid=GRID, a1_source=0, only=None):
     return ctxs
 
 
+def make_batch(storage, stream, grid=GRID, launch=None):
+    """The three lattices' shear layers as one batch (lbm_batch_*): one kernel launch per step; the
+    launch shape from the library's autotuner (run before the initial state is set), or `launch` =
+    (threads, rows per item, blocks per SM) when given."""
+    from paper_1704_04413_gb300 import lbm
+    ps, fields = [], []
+    for name, neq in LATTICES:
+        V, cs2, nu, fl = shear_fields(name, grid)
+        ps.append(lbm.make_params(name, grid, grid, nu=nu, collision="rr", hermite_order=neq, storage=storage,
+                                  stream=stream))
+        fields.append(fl)
+    b = lbm.lbm_batch_create(ps)
+    if launch:
+        lbm.lbm_batch_set_launch(b, *launch)
+    else:
+        lbm.lbm_batch_autotune(b, 3)
+    ctxs = [lbm.lbm_batch_context(b, i) for i in range(len(ps))]
+    for c, fl in zip(ctxs, fields):
+        lbm.lbm_init(c, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+    return b, ctxs
+
+
+def timed_batch_steps(b, steps, warmup, stream_t):
+    """Whole-region ms of `steps` batched steps (graph replays of the one-launch step) after `warmup`."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    lbm.lbm_batch_step(b, warmup + (warmup % 2))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.time()
+    t0.record(stream_t)
+    lbm.lbm_batch_step(b, steps)
+    t1.record(stream_t)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    return t0.elapsed_time(t1), (w0, w1)
+
+
 def timed_steps(ctxs, steps, warmup, stream_t):
     """Per-lattice kernel ms (events around each launch) and the whole-region ms."""
     import torch
@@ -258,35 +299,40 @@ def run_ours(args, rank, world, local_rank):
     peak_src = "measured" if peaks else "fallback"
     ncell = GRID * GRID
 
-    # ---- headline: FP32 compute + storage, RR, three lattices ----
-    ctxs = [make_contexts("f32", st, only=name)[0] for name in HEADLINE_ORDER]
+    # ---- headline: FP32 compute + storage, RR, the three lattices' grids as one batch (one launch a step) ----
+    b, bctx = make_batch("f32", st)
     if world > 1:
         torch.distributed.barrier()
     with Clocks(local_rank) as clk:
-        per, total_ms, window = timed_steps(ctxs, args.steps, args.warmup, stream_t)
+        total_ms, window = timed_batch_steps(b, args.steps, args.warmup, stream_t)
         clk.mark(*window)
     if world > 1:
         torch.distributed.barrier()
         t = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
+    threads, rows, bps = lbm.lbm_batch_get_launch(b)
+    lbm.lbm_batch_destroy(b)
     ms_per_step = total_ms / args.steps
-    value = len(ctxs) * ncell * args.steps * world / (total_ms * 1e-3) / 1e9
+    value = len(LATTICES) * ncell * args.steps * world / (total_ms * 1e-3) / 1e9
+    # dominant (and only) kernel of the timed region: the batched step, one launch per step
+    dom_bytes = sum(2 * V * BYTES["f32"] * ncell for V in (9, 17, 37))
+    achieved = dom_bytes / (ms_per_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": profiled_traffic(),
+                "kernel": "k_batch<RR,f32,with D2V37>: D2Q9 + D2V17 + D2V37 1024^2 in one launch",
+                "algorithmic_bytes": dom_bytes, "launch_duration_us": round(ms_per_step * 1e3, 2),
+                "launch": {"threads": threads, "rows_per_item": rows, "blocks_per_sm": bps or "one block per item"},
+                "peak_source": peak_src + " hbm_gbs (copy)"}
+    # ---- per lattice: each grid stepped by its own context (the single-grid kernels), interleaved ----
+    ctxs = [make_contexts("f32", st, only=name)[0] for name in HEADLINE_ORDER]
+    per, _, _ = timed_steps(ctxs, min(args.steps, 200), args.warmup, stream_t)
     per_lattice = {}
     for (name, V, ctx, _), ms in zip(ctxs, per):
         glups = ncell / (ms * 1e-3) / 1e9
         gbs = glups * 2 * V * BYTES["f32"]
         per_lattice[name] = {"f32": {"glups": round(glups, 3), "ms": round(ms, 5), "gbs": round(gbs, 1),
                                      "frac": round(gbs / hbm_peak, 4)}}
-    # dominant kernel: D2V37 RR FP32
-    dom_ms = per[-1]
-    dom_bytes = 2 * 37 * BYTES["f32"] * ncell
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = profiled_traffic()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
-                "kernel": "k_step<D2V37,RR,isothermal,f32,f32> 1024^2", "algorithmic_bytes": dom_bytes,
-                "peak_source": peak_src + " hbm_gbs (copy)"}
     sec = set(args.sections.split(","))
     # ---- e2e through the C ABI with host buffers (pinned), every step: init from host, step, moments to host ----
     e2e = e2e_bench(args, st, stream_t) if "e2e" in sec else None
@@ -346,16 +392,16 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "double shear layer Re=3e4 Ma=0.1 (kappa=80, delta=0.05), 1024x1024 periodic; "
-                                   "one step = lbm_step on D2Q9 (N=2), D2V17 (N=3), D2V37 (N=4), RR, FP32",
+                                   "one step = one batched launch (lbm_batch_step) over the D2Q9 (N=2), D2V17 "
+                                   "(N=3) and D2V37 (N=4) grids, RR, FP32",
                        "grid": GRID, "lattices": [n for n, _ in LATTICES], "collision": "rr",
                        "storage": "f32", "parallelism": "replicas" if world > 1 else "single",
-                       "launch_order": list(HEADLINE_ORDER),
-                       "l2": "not flushed: each lattice's buffers (75/143/310 MB) are evicted between its "
-                             "iterations by the other two lattices' traffic (528 MB > 129 MB L2)"},
+                       "l2": "not flushed: each step moves 528 MB (the three grids' 75/143/310 MB pairs of "
+                             "buffers), above the 129 MB L2"},
             "roofline": roofline, "per_lattice": per_lattice, "e2e": e2e,
             "per_lattice_4096": large, "a1_finite_difference_f32": fd, "accuracy_vs_f64_gpu": accuracy, "batched_sweep": batched,
             "learned_closure": closure, "stability_map": stab, "lattices_3d": d3,
-            "gpu_launches": len(ctxs) * args.steps, "clocks": clk.summary()}
+            "gpu_launches": args.steps, "clocks": clk.summary()}
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(min_seconds=10.0) if "cpu" in sec else None
         print(json.dumps(line), flush=True)
@@ -560,17 +606,18 @@ def vorticity(ux, uy):
     return d(uy, 1) - d(ux, 0)
 
 
-def accuracy_vs_f64(stream, L=256, storages=("f32", "f16", "bf16", "i16")):
-    """Relative L2 error of vorticity (and of rho, u) after one convective time t_c = L/u0 of the
-    shear layer, each storage format against the FP64 GPU run of the same lattice.  "f64_perturbed" is a
-    control: the FP64 run with its initial populations multiplied by (1 + eta), eta uniform in
-    [-2^-24, 2^-24] (one FP32 rounding), i.e. the divergence the flow itself gives to rounding-size noise."""
+def accuracy_vs_f64(stream, L=256, storages=("f32", "f16", "bf16", "i16"), checkpoints=8):
+    """Relative L2 error of vorticity (and of rho, u) of each storage format against the FP64 GPU run of the
+    same lattice, at `checkpoints` equally spaced times up to one convective time t_c = L/u0 of the shear
+    layer (the curve) and at t_c.  "f64_perturbed" is the control: the FP64 run with its initial
+    populations multiplied by (1 + eta), eta uniform in [-2^-24, 2^-24] (one FP32 rounding), i.e. how the
+    flow itself amplifies rounding-size noise injected once."""
     from paper_1704_04413_gb300 import lbm
     out = {}
     for name, neq in LATTICES:
         V, cs2, nu, fl = shear_fields(name, L)
         u0, _, steps = wl.shear_layer_params(L, np.sqrt(cs2), MACH, RE)
-        res = {}
+        runs = {}
         for storage in ("f64",) + tuple(storages) + ("f64_perturbed",):
             st_fmt = "f64" if storage == "f64_perturbed" else storage
             p = lbm.make_params(name, L, L, nu=nu, collision="rr", hermite_order=neq, storage=st_fmt, stream=stream)
@@ -581,20 +628,34 @@ def accuracy_vs_f64(stream, L=256, storages=("f32", "f16", "bf16", "i16")):
                 lbm.lbm_get_populations(ctx, f)
                 f *= 1.0 + wl.population_noise(V, L, L, seed=11, eps=2.0 ** -24)
                 lbm.lbm_set_populations(ctx, f)
-            lbm.lbm_step(ctx, steps)
-            r, u, v = (np.empty((L, L)) for _ in range(3))
-            lbm.lbm_moments(ctx, r, u, v)
+            runs[storage] = ctx
+        marks = [int(round(steps * (k + 1) / checkpoints)) for k in range(checkpoints)]
+        curve = {s_: [] for s_ in runs if s_ != "f64"}
+        done, final = 0, {}
+        for t in marks:
+            fields = {}
+            for storage, ctx in runs.items():
+                lbm.lbm_step(ctx, t - done)
+                r, u, v = (np.empty((L, L)) for _ in range(3))
+                lbm.lbm_moments(ctx, r, u, v)
+                fields[storage] = (r, u, v, vorticity(u, v))
+            done = t
+            r0, u0_, v0, w0 = fields["f64"]
+            for storage in curve:
+                r, u, v, w = fields[storage]
+                ok = bool(np.all(np.isfinite(w)))
+                curve[storage].append(round(float(np.linalg.norm(w - w0) / np.linalg.norm(w0)), 6) if ok else None)
+                if t == marks[-1]:
+                    final[storage] = {
+                        "vorticity_rel_l2": float(np.linalg.norm(w - w0) / np.linalg.norm(w0)) if ok else None,
+                        "u_rel_l2": float(np.linalg.norm(np.hypot(u - u0_, v - v0)) / np.linalg.norm(np.hypot(u0_, v0)))
+                        if ok else None,
+                        "rho_rel_l2": float(np.linalg.norm(r - r0) / np.linalg.norm(r0)) if ok else None}
+        for ctx in runs.values():
             lbm.lbm_destroy(ctx)
-            res[storage] = (r, u, v, vorticity(u, v))
-        r0, u0_, v0, w0 = res["f64"]
-        out[name] = {"steps": steps, "grid": L}
-        for storage in tuple(storages) + ("f64_perturbed",):
-            r, u, v, w = res[storage]
-            ok = bool(np.all(np.isfinite(w)))
-            out[name][storage] = {
-                "vorticity_rel_l2": float(np.linalg.norm(w - w0) / np.linalg.norm(w0)) if ok else None,
-                "u_rel_l2": float(np.linalg.norm(np.hypot(u - u0_, v - v0)) / np.linalg.norm(np.hypot(u0_, v0))) if ok else None,
-                "rho_rel_l2": float(np.linalg.norm(r - r0) / np.linalg.norm(r0)) if ok else None}
+        out[name] = {"steps": steps, "grid": L, "t_over_tc": [round(m / steps, 4) for m in marks]}
+        for storage in curve:
+            out[name][storage] = dict(final[storage], vorticity_rel_l2_vs_t=curve[storage])
     return out
 
 
@@ -682,6 +743,22 @@ def kernel_only(args):
     lbm.lbm_destroy(ctx)
 
 
+def headline_only(args):
+    """The timed headline alone (profiling case): the three-lattice batch with the launch shape of
+    --batch-launch (else autotuned: 16 shapes x 4 launches), `warmup` (rounded up to even) then `steps`
+    batched launches; prints ms per step."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    torch.cuda.set_device(0)
+    stream_t = torch.cuda.Stream()
+    launch = tuple(int(v) for v in args.batch_launch.split(",")) if args.batch_launch else None
+    b, _ = make_batch(args.storage, stream_t.cuda_stream, launch=launch)
+    total_ms, _ = timed_batch_steps(b, args.steps, args.warmup, stream_t)
+    t, r, q = lbm.lbm_batch_get_launch(b)
+    lbm.lbm_batch_destroy(b)
+    print(json.dumps({"headline_only": True, "ms_per_step": total_ms / args.steps, "launch": [t, r, q]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -693,6 +770,10 @@ def main():
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--batched-only", action="store_true", help="profiling case: only the batched sweep")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="profiling case: only the timed headline batch (no other section)")
+    ap.add_argument("--batch-launch", default=None, metavar="THREADS,ROWS,BLOCKS_PER_SM",
+                    help="launch shape of --headline-only instead of the autotuner's")
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
     ap.add_argument("--d3-only", action="store_true",
                     help="only the 3D lattice section (--grid3, --storage as a comma list, --lattices3)")
@@ -714,6 +795,9 @@ def main():
         return
     if args.kernel_only:
         kernel_only(args)
+        return
+    if args.headline_only:
+        headline_only(args)
         return
     if args.batched_only:
         import torch

@@ -208,16 +208,16 @@ int lbm_conservation_noalloc(int lattice, int storage, const void *f, int nx, in
                              double store_scale, double *out4, void *stream);
 
 /* ------------------------------------------------------------------------
- * Batched sweep: up to LBM_BATCH_MAX independent D2Q9 / D2V17 grids of any
- * sizes and relaxation times, mixed freely, advanced together by one kernel
- * launch per time step (recorded once in a CUDA graph of two steps and
- * replayed).  Per cell the arithmetic is that of lbm_step, so a batched step
- * is bit-identical to stepping each instance on its own.
+ * Batched sweep: up to LBM_BATCH_MAX independent D2Q9 / D2V17 / isothermal
+ * D2V37 grids of any sizes and relaxation times, mixed freely, advanced
+ * together by one kernel launch per time step (recorded once in a CUDA graph
+ * of two steps and replayed).  Per cell the arithmetic is that of lbm_step, so
+ * a batched step is bit-identical to stepping each instance on its own.
  * ------------------------------------------------------------------------ */
 #define LBM_BATCH_MAX 64
 typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
 
-/* One context per entry of ps[0..n-1] (lattice D2Q9 or D2V17, isothermal,
+/* One context per entry of ps[0..n-1] (lattice D2Q9, D2V17 or D2V37, isothermal,
  * compute LBM_F32 with any non-FP64 storage, a1 by projection; one collision model, one storage
  * format and one stream for all).  Errors as lbm_create; LBM_EINVAL for
  * n outside [1, LBM_BATCH_MAX] or mixed collision / storage / stream. */
@@ -236,13 +236,14 @@ lbm_ctx *lbm_batch_context(lbm_batch *b, int i);
 int lbm_batch_step(lbm_batch *b, int n);
 
 /* Launch shape of the batched kernel: threads per block (64, 128 or 256; each
- * thread updates two neighbouring cells), rows per work item (1..64) and
- * blocks per SM of a persistent grid (0 = one block per work item). */
+ * thread updates two neighbouring cells of D2Q9 / D2V17, one of D2V37; a batch
+ * holding D2V37 takes 128 only), rows per work item (1..64) and blocks per SM
+ * of a persistent grid (0 = one block per work item). */
 int lbm_batch_set_launch(lbm_batch *b, int threads, int rows, int blocks_per_sm);
 int lbm_batch_get_launch(const lbm_batch *b, int *threads, int *rows, int *blocks_per_sm);
 
 /* Autotuner: times every launch shape of the candidate set (threads
- * {64,128,256} x rows {1,2,4,8} x blocks per SM {0 (one per item),2,4,8}) with 1 + `steps`
+ * {64,128,256} (128 with D2V37) x rows {1,2,4,8} x blocks per SM {0 (one per item),2,4,8}) with 1 + `steps`
  * batched steps each and keeps the fastest; *best_ms (may be NULL) receives its
  * time per step.  Every timed step advances the instances, so tune before
  * lbm_init (or re-initialise afterwards).  Synchronizes. */

@@ -1,17 +1,20 @@
-// Batched stream-and-collide: many independent grids (D2Q9 and D2V17, uneven
-// sizes and relaxation times) advanced by one kernel launch per time step, the
-// launches captured in a CUDA graph (one kernel node per step).
+// Batched stream-and-collide: many independent grids (D2Q9, D2V17 and
+// isothermal D2V37, uneven sizes and relaxation times) advanced by one kernel
+// launch per time step, the launches captured in a CUDA graph (one kernel node
+// per step).
 //
-// Work item = `rows` consecutive rows x (2 * threads) columns of one
-// instance; the items of all instances are numbered consecutively, those of
-// the D2V17 instances (twice the bytes and arithmetic per cell) first, and
-// either one block per item or a persistent grid of (SMs x blocks per SM)
-// blocks walks them.  The instance table travels as a kernel parameter
+// Work item = `rows` consecutive rows x (cells per thread * threads) columns of
+// one instance (two cells per thread on D2Q9 / D2V17, one on D2V37, as the
+// single-grid kernels); the items of all instances are numbered consecutively,
+// those of the lattices with the most work per cell first (D2V37, D2V17,
+// D2Q9), and either one block per item or a persistent grid of (SMs x blocks
+// per SM) blocks walks them.  The instance table travels as a kernel parameter
 // (constant bank); each item finds its instance by a binary search over the
 // first-item offsets and takes that instance's lattice (a block-uniform
-// branch).  Per cell the arithmetic is the single-grid two-cell kernel's
-// (step2_cells), so a batched step is bitwise identical to per-instance
-// lbm_step calls.
+// branch).  Per cell the arithmetic is the single-grid kernels' (step2_cells,
+// step_cell), so a batched step is bitwise identical to per-instance lbm_step
+// calls.  A batch holding D2V37 runs 128-thread blocks at the D2V37 kernel's
+// register cap (72, seven blocks a SM).
 //
 // The launch shape (threads per block, rows per item, blocks per SM) is chosen
 // by lbm_batch_autotune, which times every candidate on the batch itself.
@@ -35,7 +38,7 @@ struct BatchInst {
   StepGeom g;
   CollParams<F2> P;
   int ntx;         // items per row band
-  int lattice;     // LBM_D2Q9 or LBM_D2V17
+  int lattice;     // LBM_D2Q9, LBM_D2V17 or LBM_D2V37
   long long item0; // first work item of the instance
 };
 
@@ -59,8 +62,34 @@ __device__ __forceinline__ void batch_item(const BatchInst& I, int rows, int ban
   }
 }
 
+// The rows of one work item of a D2V37 instance, one cell per thread.
 template <int COLL, class S>
-__global__ void __launch_bounds__(256, 1) k_batch(const __grid_constant__ BatchDesc d) {
+__device__ __forceinline__ void batch_item_v37(const BatchInst& I, int rows, int band, int x) {
+  const S* fin = static_cast<const S*>(I.fin);
+  S* fout = static_cast<S*>(I.fout);
+  const GeomOffsets<D2V37, S> off{I.g.plane * (long long)sizeof(S), (long long)I.g.pitch * (long long)sizeof(S)};
+  CollParams<float> P;  // both lanes of the pair parameters hold the same values
+  P.omega = I.P.omega.v.x;
+  P.om1 = I.P.om1.v.x;
+  P.om1_3 = I.P.om1_3.v.x;
+  P.om1_4 = I.P.om1_4.v.x;
+  P.tau = I.P.tau.v.x;
+  P.tau3 = I.P.tau3.v.x;
+  P.neq = I.P.neq;
+  P.nreg = I.P.nreg;
+  P.rho0 = I.P.rho0.v.x;
+  P.s = I.P.s.v.x;
+  P.inv_s = I.P.inv_s.v.x;
+  for (int r = 0; r < rows; ++r) {
+    const int y = band * rows + r;
+    if (y >= I.g.ny) break;
+    step_cell<D2V37, COLL, false, float, S, false>(fin, fout, I.g, P, off, nullptr, x, y);
+  }
+}
+
+// V37: the batch holds D2V37 instances (128-thread blocks, the register cap of the D2V37 kernel).
+template <int COLL, class S, bool V37>
+__global__ void __launch_bounds__(V37 ? 128 : 256, V37 ? 7 : 1) k_batch(const __grid_constant__ BatchDesc d) {
   for (long long it = blockIdx.x; it < d.total; it += gridDim.x) {
     int lo = 0, hi = d.n - 1;
     while (lo < hi) {
@@ -71,6 +100,13 @@ __global__ void __launch_bounds__(256, 1) k_batch(const __grid_constant__ BatchD
     const long long local = it - I.item0;
     const int band = (int)(local / I.ntx);
     const int tx = (int)(local - (long long)band * I.ntx);
+    if constexpr (V37) {
+      if (I.lattice == LBM_D2V37) {
+        const int x = tx * (int)blockDim.x + (int)threadIdx.x;
+        if (x < I.g.nx) batch_item_v37<COLL, S>(I, d.rows, band, x);
+        continue;
+      }
+    }
     const int x = 2 * (tx * (int)blockDim.x + (int)threadIdx.x);
     const int xw = 2 * (tx * (int)blockDim.x + (int)(threadIdx.x & ~31u));
     if (x >= I.g.nx) continue;
@@ -88,7 +124,14 @@ cudaError_t batch_launch_t(const BatchDesc& d, int threads, int blocks_per_sm, i
   long long grid = blocks_per_sm > 0 ? (long long)blocks_per_sm * nsm : d.total;
   if (grid > d.total) grid = d.total;
   if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
-  k_batch<COLL, S><<<(unsigned)grid, threads, 0, st>>>(d);
+  bool v37 = false;
+  for (int k = 0; k < d.n; ++k) v37 = v37 || d.inst[k].lattice == LBM_D2V37;
+  if (v37) {
+    if (threads != 128) return cudaErrorInvalidValue;
+    k_batch<COLL, S, true><<<(unsigned)grid, threads, 0, st>>>(d);
+  } else {
+    k_batch<COLL, S, false><<<(unsigned)grid, threads, 0, st>>>(d);
+  }
   return cudaGetLastError();
 }
 
@@ -121,6 +164,7 @@ struct lbm_batch {
   lbm_ctx* ctx[kBatchMax] = {nullptr};
   int coll = 0, prec = 0;
   int threads = 128, rows = 1, blocks_per_sm = 0;  // launch shape (0 = as many as fit)
+  bool v37 = false;                                 // holds D2V37 instances: 128-thread blocks only
   cudaStream_t st = nullptr;       // the instances' stream
   cudaStream_t capture = nullptr;  // private stream used to record the graph
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps, from parity 0 / 1 of the first instance
@@ -130,13 +174,14 @@ struct lbm_batch {
 
 namespace {
 
-// Launch descriptor of every instance, each reading buffer cur ^ flip: the D2V17 instances' items first.
+// Launch descriptor of every instance, each reading buffer cur ^ flip: the items of D2V37, then D2V17,
+// then D2Q9 instances.
 BatchDesc make_desc(const lbm_batch* b, int flip) {
   BatchDesc d{};
   d.n = 0;
   d.rows = b->rows;
   long long item = 0;
-  for (int lattice : {LBM_D2V17, LBM_D2Q9})
+  for (int lattice : {LBM_D2V37, LBM_D2V17, LBM_D2Q9})
     for (int k = 0; k < b->n; ++k) {
       const lbm_ctx* c = b->ctx[k];
       if (c->p.lattice != lattice) continue;
@@ -146,7 +191,8 @@ BatchDesc make_desc(const lbm_batch* b, int flip) {
       I.fout = c->buf[cur ^ 1];
       I.g = c->g;
       I.P = cast_params<F2>(lbm_ctx_coll_params(c));
-      I.ntx = (c->p.nx + 2 * b->threads - 1) / (2 * b->threads);
+      const int cells = lattice == LBM_D2V37 ? b->threads : 2 * b->threads;  // columns of an item
+      I.ntx = (c->p.nx + cells - 1) / cells;
       I.lattice = lattice;
       I.item0 = item;
       item += (long long)I.ntx * ((c->p.ny + b->rows - 1) / b->rows);
@@ -199,7 +245,7 @@ int lbm_batch_create(const lbm_params* ps, int n, lbm_batch** out) {
   if (!ps || n < 1 || n > kBatchMax) return LBM_EINVAL;
   for (int k = 0; k < n; ++k) {
     const lbm_params& p = ps[k];
-    if (p.lattice != LBM_D2Q9 && p.lattice != LBM_D2V17) return LBM_EINVAL;
+    if (p.lattice != LBM_D2Q9 && p.lattice != LBM_D2V17 && p.lattice != LBM_D2V37) return LBM_EINVAL;
     if (p.thermal || p.compute != LBM_F32 || p.storage == LBM_F64) return LBM_EINVAL;
     if (p.a1_source != LBM_A1_PROJECTION) return LBM_EINVAL;  // the batched kernel projects a1
     if (p.collision != ps[0].collision || p.storage != ps[0].storage || p.stream != ps[0].stream) return LBM_EINVAL;
@@ -215,6 +261,7 @@ int lbm_batch_create(const lbm_params* ps, int n, lbm_batch** out) {
     }
   }
   b->n = n;
+  for (int k = 0; k < n; ++k) b->v37 = b->v37 || ps[k].lattice == LBM_D2V37;
   b->coll = ps[0].collision;
   b->prec = b->ctx[0]->prec;
   b->st = static_cast<cudaStream_t>(ps[0].stream);
@@ -266,6 +313,7 @@ int lbm_batch_step(lbm_batch* b, int n) {
 int lbm_batch_set_launch(lbm_batch* b, int threads, int rows, int blocks_per_sm) {
   if (!b || (threads != 64 && threads != 128 && threads != 256) || rows < 1 || rows > 64 || blocks_per_sm < 0)
     return LBM_EINVAL;
+  if (b->v37 && threads != 128) return LBM_EINVAL;
   b->threads = threads;
   b->rows = rows;
   b->blocks_per_sm = blocks_per_sm;
@@ -294,6 +342,7 @@ int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms) {
   int rc = LBM_OK;
   for (int t : threads_c)
     for (int r : rows_c)
+      if (!b->v37 || t == 128)
       for (int q : bps_c) {
         b->threads = t;
         b->rows = r;

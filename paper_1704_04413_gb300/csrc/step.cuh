@@ -88,6 +88,28 @@ struct PullOffsets {
   int cy[Q];  // y-velocity components, indexed at run time by the staged kernel's copy-issuing lanes
 };
 
+// Offsets of the pulled source / the store of population i as template accessors: from the kernel
+// parameters (single-grid launches) or recomputed from the grid geometry (batched launches).
+template <int Q>
+struct ParamOffsets {
+  const PullOffsets<Q>& o;
+  template <int i>
+  __device__ __forceinline__ long long src() const { return o.src[i]; }
+  template <int i>
+  __device__ __forceinline__ long long dst() const { return o.dst[i]; }
+};
+template <class L, class S>
+struct GeomOffsets {
+  long long plane_b, pitch_b;  // bytes
+  template <int i>
+  __device__ __forceinline__ long long src() const {
+    constexpr int cx = L::CX[i], cy = L::CY[i];
+    return i * plane_b - cy * pitch_b - cx * (long long)sizeof(S);
+  }
+  template <int i>
+  __device__ __forceinline__ long long dst() const { return i * plane_b; }
+};
+
 // Raw loads issued in program order (volatile asm keeps them ahead of the arithmetic that consumes
 // them, so all V loads of a cell are in flight together).
 template <class S>
@@ -137,9 +159,9 @@ struct StepBlocks {
 // FD: a1 from central differences of the moments field mom[4][ny][nx] (rho, ux, uy, theta after streaming;
 // the pass k_stream_moments writes it); neighbours follow the streaming rule (periodic wrap, or the
 // clamped edge cell on a zero-gradient axis).
-template <class L, int COLL, bool THERMAL, class Real, class S, bool FD>
+template <class L, int COLL, bool THERMAL, class Real, class S, bool FD, class OFF>
 __device__ __forceinline__ void step_cell(const S* __restrict__ fin, S* __restrict__ fout, const StepGeom& g,
-                                          const CollParams<Real>& P, const PullOffsets<L::Q>& off,
+                                          const CollParams<Real>& P, const OFF& off,
                                           const Real* __restrict__ mom, int x, int y) {
   const long long cen = (long long)y * g.pitch + x;
   Real q[L::Q];
@@ -167,7 +189,7 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ fin, S* __restri
     });
     sfor<0, L::Q>([&](auto I) {
       constexpr int i = LBM_CI(I);
-      q[i] = (Real)ld_raw<S>(cb[L::CX[i] + L::VMAX] + off.src[i]);
+      q[i] = (Real)ld_raw<S>(cb[L::CX[i] + L::VMAX] + off.template src<i>());
     });
   } else {
     const char* b = reinterpret_cast<const char*>(fin);
@@ -175,7 +197,7 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ fin, S* __restri
       constexpr int i = LBM_CI(I);
       const int xs = src_coord(x, L::CX[i], g.nx, g.bcx);
       const int ys = src_coord(y, L::CY[i], g.ny, g.bcy);
-      q[i] = (Real)ld_raw<S>(b + off.dst[i] + ((long long)ys * g.pitch + xs) * (long long)sizeof(S));
+      q[i] = (Real)ld_raw<S>(b + off.template dst<i>() + ((long long)ys * g.pitch + xs) * (long long)sizeof(S));
     });
   }
   Real grad[6];
@@ -197,7 +219,7 @@ __device__ __forceinline__ void step_cell(const S* __restrict__ fin, S* __restri
   char* o = reinterpret_cast<char*>(fout + cen);
   sfor<0, L::Q>([&](auto I) {
     constexpr int i = LBM_CI(I);
-    Store<S>::st(reinterpret_cast<S*>(o + off.dst[i]), q[i]);
+    Store<S>::st(reinterpret_cast<S*>(o + off.template dst<i>()), q[i]);
   });
 }
 
@@ -212,7 +234,7 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L, THERMAL, Real>::MIN)
   const int bx = blockIdx.x - y * nbx;
   const int x = bx * STEP_BX + threadIdx.x;
   if (x >= g.nx) return;
-  step_cell<L, COLL, THERMAL, Real, S, FD>(fin, fout, g, P, off, mom, x, y);
+  step_cell<L, COLL, THERMAL, Real, S, FD>(fin, fout, g, P, ParamOffsets<L::Q>{off}, mom, x, y);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,28 +319,6 @@ template <class L, class S>
 struct Step2Blocks {
   static constexpr int MIN =
       L::Q > 20 ? (std::is_same<S, __half>::value ? LBM_STEP2_MINB_LARGE_F16 : LBM_STEP2_MINB_LARGE) : 1;
-};
-
-// Offsets of the pulled source / the store of population i as template accessors: from the kernel
-// parameters (single-grid launches) or recomputed from the grid geometry (batched launches).
-template <int Q>
-struct ParamOffsets {
-  const PullOffsets<Q>& o;
-  template <int i>
-  __device__ __forceinline__ long long src() const { return o.src[i]; }
-  template <int i>
-  __device__ __forceinline__ long long dst() const { return o.dst[i]; }
-};
-template <class L, class S>
-struct GeomOffsets {
-  long long plane_b, pitch_b;  // bytes
-  template <int i>
-  __device__ __forceinline__ long long src() const {
-    constexpr int cx = L::CX[i], cy = L::CY[i];
-    return i * plane_b - cy * pitch_b - cx * (long long)sizeof(S);
-  }
-  template <int i>
-  __device__ __forceinline__ long long dst() const { return i * plane_b; }
 };
 
 // Two neighbouring cells (x, x+1) of row y: pull, collide, store.  xw is the first column of the
@@ -475,7 +475,10 @@ struct Stage2 {
   static constexpr int MIN_BLOCKS = L::Q <= 9 ? 5 : 4;
 };
 
-template <class L, int COLL, class S>
+// WHOLE: every row fits one tile (nbt == 1) and the x wrap is an index inside the staged row; otherwise
+// the staged rows carry PAD cells of margin (edge tiles copy the wrapped columns), so the staged source of
+// population i for cell x sits at a compile-time offset -c_x from the cell's own slot.
+template <class L, int COLL, class S, bool WHOLE>
 __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCKS)
     k_step2_staged(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbt, long long ntiles,
                    CollParams<F2> P, const __grid_constant__ PullOffsets<L::Q> off, StageCtl ctl) {
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
     mbar_init_fence();
   }
   __syncthreads();
-  const bool whole_rows = nbt == 1;
+  constexpr bool whole_rows = WHOLE;
   const long long t_begin = blockIdx.x * ntiles / gridDim.x;
   const int n_mine = (int)((blockIdx.x + 1LL) * ntiles / gridDim.x - t_begin);
   const int y_begin = (int)(t_begin / nbt), bx_begin = (int)(t_begin - (long long)y_begin * nbt);
@@ -565,29 +568,42 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
       const bool two = x + 1 < g.nx;
       F2 q[L::Q];
       if (active) {
-        // staged positions of the pulled sources x - cx and x + 1 - cx, per x-velocity; an even cx moves
-        // both cells of the pair together (x is even), so it is one aligned vector read
-        int pos0[2 * L::VMAX + 1], pos1[2 * L::VMAX + 1];
-        sfor<0, 2 * L::VMAX + 1>([&](auto J) {
-          constexpr int j = LBM_CI(J);
-          int xs0 = x - (j - L::VMAX), xs1 = x + 1 - (j - L::VMAX);
-          if (whole_rows) {
+        // staged positions of the pulled sources x - cx and x + 1 - cx; an even cx moves both cells of the
+        // pair together (x is even), so it is one aligned vector read
+        const S* row0 = sp + (x - x0 + St::PAD);
+        if constexpr (WHOLE) {
+          // the row is staged whole: wrap x - cx by index, one base per x-velocity
+          int pos0[2 * L::VMAX + 1], pos1[2 * L::VMAX + 1];
+          sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+            constexpr int j = LBM_CI(J);
+            int xs0 = x - (j - L::VMAX), xs1 = x + 1 - (j - L::VMAX);
             xs0 += (xs0 < 0 ? g.nx : 0) - (xs0 >= g.nx ? g.nx : 0);
             xs1 += (xs1 < 0 ? g.nx : 0) - (xs1 >= g.nx ? g.nx : 0);
-          }
-          pos0[j] = xs0 - x0 + St::PAD;
-          pos1[j] = xs1 - x0 + St::PAD;
-        });
-        sfor<0, L::Q>([&](auto I) {
-          constexpr int i = LBM_CI(I);
-          constexpr int j = L::CX[i] + L::VMAX;
-          const S* row = sp + i * St::W;
-          if constexpr (L::CX[i] % 2 == 0) {
-            q[i] = sm_pair<S>(row + pos0[j]);
-          } else {
-            q[i] = F2(sm_decode<S>(row[pos0[j]]), sm_decode<S>(row[pos1[j]]));
-          }
-        });
+            pos0[j] = xs0 - x0 + St::PAD;
+            pos1[j] = xs1 - x0 + St::PAD;
+          });
+          sfor<0, L::Q>([&](auto I) {
+            constexpr int i = LBM_CI(I);
+            constexpr int j = L::CX[i] + L::VMAX;
+            const S* row = sp + i * St::W;
+            if constexpr (L::CX[i] % 2 == 0) {
+              q[i] = sm_pair<S>(row + pos0[j]);
+            } else {
+              q[i] = F2(sm_decode<S>(row[pos0[j]]), sm_decode<S>(row[pos1[j]]));
+            }
+          });
+        } else {
+          // margins hold the wrapped columns: population i's source is row0 + i W - c_x (immediates)
+          sfor<0, L::Q>([&](auto I) {
+            constexpr int i = LBM_CI(I);
+            constexpr int o = i * St::W - L::CX[i];
+            if constexpr (L::CX[i] % 2 == 0) {
+              q[i] = sm_pair<S>(row0 + o);
+            } else {
+              q[i] = F2(sm_decode<S>(row0[o]), sm_decode<S>(row0[o + 1]));
+            }
+          });
+        }
       }
       if constexpr (pr == St::PAIRS - 1) {
         __syncwarp();
@@ -617,14 +633,14 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
 }
 
 // Blocks of the staged pair kernel resident per SM, times the SM count (per device, taken once).
-template <class L, int COLL, class S>
+template <class L, int COLL, class S, bool WHOLE>
 inline int staged2_grid(int* out) {
   static int dev_cached = -1, grid_cached = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
   if (dev != dev_cached) {
-    auto k = k_step2_staged<L, COLL, S>;
+    auto k = k_step2_staged<L, COLL, S, WHOLE>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage2<L, S>::SMEM);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0, sms = 0;
@@ -655,11 +671,15 @@ inline cudaError_t launch_step2_t(const void* fin, void* fout, const StepGeom& g
     const int nbt = (g.nx + St::BXT - 1) / St::BXT;
     const long long ntiles = (long long)nbt * g.ny;
     int grid = 0;
-    const int e = staged2_grid<L, COLL, S>(&grid);
+    const int e = nbt == 1 ? staged2_grid<L, COLL, S, true>(&grid) : staged2_grid<L, COLL, S, false>(&grid);
     if (e) return (cudaError_t)e;
     const long long nb = ntiles < grid ? ntiles : grid;
-    k_step2_staged<L, COLL, S><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
-        (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+    if (nbt == 1)
+      k_step2_staged<L, COLL, S, true><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
+          (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+    else
+      k_step2_staged<L, COLL, S, false><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
+          (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
     return cudaGetLastError();
     }
   }

@@ -18,18 +18,23 @@ SHAPES = [("D2Q9", 130, 70, 2e4), ("D2V17", 96, 64, 5e4), ("D2Q9", 300, 33, 1e5)
           ("D2Q9", 64, 64, 1e4), ("D2V17", 190, 41, 1e6)]
 
 
-def params(m, storage):
+# with D2V37 (one cell per thread, 128-thread blocks): the three lattices of the benchmark's batched step
+SHAPES37 = [("D2V37", 150, 33, 3e4), ("D2Q9", 96, 40, 1e4), ("D2V17", 130, 21, 5e4), ("D2V37", 64, 17, 1e5)]
+NEQ = {"D2Q9": 2, "D2V17": 3, "D2V37": 4}
+
+
+def params(m, storage, shapes=SHAPES):
     out = []
-    for name, nx, ny, re in SHAPES:
+    for name, nx, ny, re in shapes:
         cs2 = orc.lattice(name).cs2
         u0, nu, _ = wl.shear_layer_params(nx, np.sqrt(cs2), 0.1, re)
-        out.append(m.make_params(name, nx, ny, nu=nu, collision="rr", hermite_order={"D2Q9": 2, "D2V17": 3}[name],
+        out.append(m.make_params(name, nx, ny, nu=nu, collision="rr", hermite_order=NEQ[name],
                                  storage=storage, stream=stream()))
     return out
 
 
-def init_all(m, ctxs):
-    for (name, nx, ny, re), c in zip(SHAPES, ctxs):
+def init_all(m, ctxs, shapes=SHAPES):
+    for (name, nx, ny, re), c in zip(shapes, ctxs):
         cs2 = orc.lattice(name).cs2
         u0, _, _ = wl.shear_layer_params(nx, np.sqrt(cs2), 0.1, re)
         fl = wl.double_shear_layer(nx, u0, ny=ny)
@@ -140,3 +145,48 @@ def test_batched_steps_match_oracle(storage, tol, blocks_per_sm):
                 assert np.max(np.abs(got - ref) / w) <= steps * tol * np.abs(f0 / w - 1.0).max(), (name, nx, ny)
     finally:
         m.lbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_with_d2v37_equals_single_steps_and_oracle(storage):
+    """D2V37 instances (one cell per thread) batched with D2Q9 and D2V17 ones: bitwise equal to per-instance
+    steps after 5 steps (graph replays and a direct launch), and every instance against three oracle
+    steps from the same populations."""
+    m = lib()
+    ps = params(m, storage, SHAPES37)
+    b = m.lbm_batch_create(ps)
+    singles = [m.lbm_create(p) for p in ps]
+    try:
+        with pytest.raises(m.LbmError):
+            m.lbm_batch_set_launch(b, 256, 1, 0)  # a batch holding D2V37 runs 128-thread blocks
+        m.lbm_batch_set_launch(b, 128, 3, 0)
+        bc = [m.lbm_batch_context(b, i) for i in range(len(ps))]
+        init_all(m, bc, SHAPES37)
+        init_all(m, singles, SHAPES37)
+        m.lbm_batch_step(b, 5)
+        for c in singles:
+            m.lbm_step(c, 5)
+        for (name, nx, ny, _), c0, c1 in zip(SHAPES37, bc, singles):
+            assert np.array_equal(pops(m, c0, name, nx, ny), pops(m, c1, name, nx, ny)), name
+        refs = []
+        for (name, nx, ny, re), i in zip(SHAPES37, range(len(ps))):
+            Lt = orc.lattice(name)
+            op = orc.params(name, nx, ny, m.lbm_tau(bc[i]), "rr", NEQ[name])
+            fl = wl.random_fields(nx, ny, 200 + i, u_scale=0.06)
+            f = orc.init(op, fl.rho, fl.ux, fl.uy) * (1.0 + wl.population_noise(Lt.V, nx, ny, 300 + i, 0.01))
+            m.lbm_set_populations(bc[i], np.ascontiguousarray(f[perm(name)]))
+            refs.append((f, orc.step(op, stored(f, storage), 3)))
+        m.lbm_batch_step(b, 3)
+        for (name, nx, ny, _), c, (f0, ref) in zip(SHAPES37, bc, refs):
+            Lt = orc.lattice(name)
+            got = np.empty_like(ref)
+            got[perm(name)] = pops(m, c, name, nx, ny)
+            if storage == "f32":
+                assert pop_rel(got, ref, Lt.w) <= 3e-6, name
+            else:
+                w = Lt.w[:, None, None]
+                assert np.max(np.abs(got - ref) / w) <= 3 * 2e-3 * np.abs(f0 / w - 1.0).max(), name
+    finally:
+        m.lbm_batch_destroy(b)
+        for c in singles:
+            m.lbm_destroy(c)
