@@ -123,7 +123,8 @@ template <class L, int COLL, bool SHIFTED, class Real>
 __device__ __forceinline__ void collide3(Real (&q)[L::Q], const CollParams<Real>& P) {
   using Sc = typename Scalar<Real>::type;
   constexpr double c2 = L::CS2;
-  constexpr int PM = COLL == COLL_PR ? L::NMAX : (COLL == COLL_RR ? 2 : 1);
+  // highest monomial order the mode needs (PR's projections of order >= 3 are summed directly, hmom_direct)
+  constexpr int PM = COLL == COLL_PR ? 2 : (COLL == COLL_RR ? 2 : 1);
   const Real rho_ref = SHIFTED ? P.rho0 : Real(1);
 
   Real d[L::Q];
@@ -173,6 +174,26 @@ __device__ __forceinline__ void collide3(Real (&q)[L::Q], const CollParams<Real>
       });
     });
     if constexpr (!SHIFTED) {
+      constexpr double kp = kappa3<L, Sc>(a, b, c);
+      if constexpr (kp != 0.0) acc += Real(kp);
+    }
+    return acc;
+  };
+
+  // Hermite moment summed directly over the populations (PR at orders >= 3): the monomial route would
+  // subtract rounded sums of the slow populations' large deviations (He_3 = c^3 - 3 cs^2 c, ...)
+  auto hmom_direct = [&](auto Aa, auto Bb, auto Cc) -> Real {
+    constexpr int a = LBM_CI(Aa), b = LBM_CI(Bb), c = LBM_CI(Cc);
+    Real acc = Real(0);
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      constexpr double h = he(a, L::CX[i], c2) * he(b, L::CY[i], c2) * he(c, L::CZ[i], c2) *
+                           (SHIFTED ? L::W[i] : 1.0);
+      if constexpr (h != 0.0) acc = madd(Real(h), d[i], acc);
+    });
+    if constexpr (SHIFTED) {
+      acc = acc * P.inv_s;
+    } else {
       constexpr double kp = kappa3<L, Sc>(a, b, c);
       if constexpr (kp != 0.0) acc += Real(kp);
     }
@@ -262,7 +283,11 @@ __device__ __forceinline__ void collide3(Real (&q)[L::Q], const CollParams<Real>
             } else if constexpr (COLL == COLL_PR && n >= 2) {
               // a1 = sum_i H (f_i - f^(0)_i) (Sec. II.E): the projection of f minus that of the truncated
               // equilibrium, sum over the kept (d, e, f) of order <= N_eq of gram3 * a0_(d,e,f)
-              Real a1 = hmom(IC<a>{}, IC<b>{}, IC<c>{});
+              Real a1;
+              if constexpr (n <= 2)
+                a1 = hmom(IC<a>{}, IC<b>{}, IC<c>{});
+              else
+                a1 = hmom_direct(IC<a>{}, IC<b>{}, IC<c>{});
               sfor<0, 5>([&](auto Dd) {
                 constexpr int d = LBM_CI(Dd);
                 sfor<0, 5>([&](auto Ee) {
