@@ -475,10 +475,14 @@ struct Stage2 {
   static constexpr int MIN_BLOCKS = L::Q <= 9 ? 5 : 4;
 };
 
-// WHOLE: every row fits one tile (nbt == 1) and the x wrap is an index inside the staged row; otherwise
-// the staged rows carry PAD cells of margin (edge tiles copy the wrapped columns), so the staged source of
-// population i for cell x sits at a compile-time offset -c_x from the cell's own slot.
-template <class L, int COLL, class S, bool WHOLE>
+// ROWS: how the staged rows hold the x wrap.  ROWS_WHOLE: every row fits one tile (nbt == 1) and the wrap is
+// an index inside the staged row.  ROWS_MARGIN: the staged rows carry PAD cells of margin (edge tiles copy
+// the wrapped columns), so the staged source of population i for cell x sits at a compile-time offset -c_x
+// from the cell's own slot.  ROWS_ANY: decided at run time from nbt, one staged position per x-velocity
+// (the form D2V17 runs fastest in: 83.4 GLUPS at 4096^2 with binary16, against 80.9 with the two
+// compile-time forms; D2Q9 takes those: 131 -> 139).
+enum { ROWS_ANY = 0, ROWS_WHOLE = 1, ROWS_MARGIN = 2 };
+template <class L, int COLL, class S, int ROWS>
 __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCKS)
     k_step2_staged(const S* __restrict__ fin, S* __restrict__ fout, StepGeom g, int nbt, long long ntiles,
                    CollParams<F2> P, const __grid_constant__ PullOffsets<L::Q> off, StageCtl ctl) {
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
     mbar_init_fence();
   }
   __syncthreads();
-  constexpr bool whole_rows = WHOLE;
+  const bool whole_rows = ROWS == ROWS_ANY ? nbt == 1 : ROWS == ROWS_WHOLE;
   const long long t_begin = blockIdx.x * ntiles / gridDim.x;
   const int n_mine = (int)((blockIdx.x + 1LL) * ntiles / gridDim.x - t_begin);
   const int y_begin = (int)(t_begin / nbt), bx_begin = (int)(t_begin - (long long)y_begin * nbt);
@@ -571,14 +575,27 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
         // staged positions of the pulled sources x - cx and x + 1 - cx; an even cx moves both cells of the
         // pair together (x is even), so it is one aligned vector read
         const S* row0 = sp + (x - x0 + St::PAD);
-        if constexpr (WHOLE) {
-          // the row is staged whole: wrap x - cx by index, one base per x-velocity
+        if constexpr (ROWS == ROWS_MARGIN) {
+          // margins hold the wrapped columns: population i's source is row0 + i W - c_x (immediates)
+          sfor<0, L::Q>([&](auto I) {
+            constexpr int i = LBM_CI(I);
+            constexpr int o = i * St::W - L::CX[i];
+            if constexpr (L::CX[i] % 2 == 0) {
+              q[i] = sm_pair<S>(row0 + o);
+            } else {
+              q[i] = F2(sm_decode<S>(row0[o]), sm_decode<S>(row0[o + 1]));
+            }
+          });
+        } else {
+          // one staged position per x-velocity, the wrap by index when the row is staged whole
           int pos0[2 * L::VMAX + 1], pos1[2 * L::VMAX + 1];
           sfor<0, 2 * L::VMAX + 1>([&](auto J) {
             constexpr int j = LBM_CI(J);
             int xs0 = x - (j - L::VMAX), xs1 = x + 1 - (j - L::VMAX);
-            xs0 += (xs0 < 0 ? g.nx : 0) - (xs0 >= g.nx ? g.nx : 0);
-            xs1 += (xs1 < 0 ? g.nx : 0) - (xs1 >= g.nx ? g.nx : 0);
+            if (whole_rows) {
+              xs0 += (xs0 < 0 ? g.nx : 0) - (xs0 >= g.nx ? g.nx : 0);
+              xs1 += (xs1 < 0 ? g.nx : 0) - (xs1 >= g.nx ? g.nx : 0);
+            }
             pos0[j] = xs0 - x0 + St::PAD;
             pos1[j] = xs1 - x0 + St::PAD;
           });
@@ -590,17 +607,6 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
               q[i] = sm_pair<S>(row + pos0[j]);
             } else {
               q[i] = F2(sm_decode<S>(row[pos0[j]]), sm_decode<S>(row[pos1[j]]));
-            }
-          });
-        } else {
-          // margins hold the wrapped columns: population i's source is row0 + i W - c_x (immediates)
-          sfor<0, L::Q>([&](auto I) {
-            constexpr int i = LBM_CI(I);
-            constexpr int o = i * St::W - L::CX[i];
-            if constexpr (L::CX[i] % 2 == 0) {
-              q[i] = sm_pair<S>(row0 + o);
-            } else {
-              q[i] = F2(sm_decode<S>(row0[o]), sm_decode<S>(row0[o + 1]));
             }
           });
         }
@@ -633,14 +639,14 @@ __global__ void __launch_bounds__(Stage2<L, S>::THREADS, Stage2<L, S>::MIN_BLOCK
 }
 
 // Blocks of the staged pair kernel resident per SM, times the SM count (per device, taken once).
-template <class L, int COLL, class S, bool WHOLE>
+template <class L, int COLL, class S, int ROWS>
 inline int staged2_grid(int* out) {
   static int dev_cached = -1, grid_cached = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return (int)e;
   if (dev != dev_cached) {
-    auto k = k_step2_staged<L, COLL, S, WHOLE>;
+    auto k = k_step2_staged<L, COLL, S, ROWS>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage2<L, S>::SMEM);
     if (e != cudaSuccess) return (int)e;
     int per_sm = 0, sms = 0;
@@ -671,15 +677,23 @@ inline cudaError_t launch_step2_t(const void* fin, void* fout, const StepGeom& g
     const int nbt = (g.nx + St::BXT - 1) / St::BXT;
     const long long ntiles = (long long)nbt * g.ny;
     int grid = 0;
-    const int e = nbt == 1 ? staged2_grid<L, COLL, S, true>(&grid) : staged2_grid<L, COLL, S, false>(&grid);
-    if (e) return (cudaError_t)e;
-    const long long nb = ntiles < grid ? ntiles : grid;
-    if (nbt == 1)
-      k_step2_staged<L, COLL, S, true><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
+    if constexpr (L::Q <= 9) {
+      const int e = nbt == 1 ? staged2_grid<L, COLL, S, ROWS_WHOLE>(&grid) : staged2_grid<L, COLL, S, ROWS_MARGIN>(&grid);
+      if (e) return (cudaError_t)e;
+      const long long nb = ntiles < grid ? ntiles : grid;
+      if (nbt == 1)
+        k_step2_staged<L, COLL, S, ROWS_WHOLE><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
+            (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+      else
+        k_step2_staged<L, COLL, S, ROWS_MARGIN><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
+            (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+    } else {
+      const int e = staged2_grid<L, COLL, S, ROWS_ANY>(&grid);
+      if (e) return (cudaError_t)e;
+      const long long nb = ntiles < grid ? ntiles : grid;
+      k_step2_staged<L, COLL, S, ROWS_ANY><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
           (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
-    else
-      k_step2_staged<L, COLL, S, false><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
-          (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+    }
     return cudaGetLastError();
     }
   }
