@@ -58,7 +58,7 @@ __device__ __forceinline__ void batch_item(const BatchInst& I, int rows, int ban
   for (int r = 0; r < rows; ++r) {
     const int y = band * rows + r;
     if (y >= I.g.ny) break;
-    step2_cells<L, COLL, S>(fin, fout, I.g, I.P, off, x, y, xw);
+    step2_cells<L, COLL, S, GeomOffsets<L, S>, true>(fin, fout, I.g, I.P, off, x, y, xw);
   }
 }
 

@@ -11,6 +11,7 @@
 // 1 / (a! b! cs^2(a+b)).  All lattice-dependent numbers are compile-time
 // constants (lattice.cuh); loops over populations and orders are unrolled.
 #pragma once
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -198,6 +199,56 @@ __device__ __forceinline__ void rebuild(const Real (&C)[5][5], F&& emit) {
   });
 }
 
+template <class L, bool SHIFTED, class Real, class F>
+__device__ __forceinline__ void rebuild_rows(const Real (&C)[5][5], F&& emit) {
+  constexpr double c2 = L::CS2;
+  constexpr int V = L::VMAX;
+  // rebuild() one row pair +-v at a time: its g[a](+-v) are made, its populations emitted, and the g die,
+  // so that a caller storing each emitted population at once never holds more than one row pair's g
+  sfor<0, V + 1>([&](auto VV) {
+    constexpr int v = LBM_CI(VV);
+    if constexpr (has_row<L>(v) || has_row<L>(-v)) {
+      Real gp[5], gm[5];
+      sfor<0, L::NMAX + 1>([&](auto Aa) {
+        constexpr int a = LBM_CI(Aa);
+        if constexpr (L::keep(a, 0)) {
+          Real ev = Real(0), od = Real(0);
+          sfor<0, L::NMAX + 1 - a>([&](auto Bb) {
+            constexpr int b = LBM_CI(Bb);
+            constexpr double h = he(b, v, c2);
+            if constexpr (L::keep(a, b) && h != 0.0) {
+              if constexpr (b % 2 == 0)
+                ev = madd(Real(h), C[a][b], ev);
+              else
+                od = madd(Real(h), C[a][b], od);
+            }
+          });
+          gp[a] = ev + od;
+          if constexpr (v != 0) gm[a] = ev - od;
+        }
+      });
+      sfor<0, L::Q>([&](auto I) {
+        constexpr int i = LBM_CI(I);
+        if constexpr (L::CY[i] == v || (v != 0 && L::CY[i] == -v)) {
+          constexpr bool up = L::CY[i] == v;
+          Real acc = Real(0);
+          sfor<0, L::NMAX + 1>([&](auto Aa) {
+            constexpr int a = LBM_CI(Aa);
+            constexpr double h = he(a, L::CX[i], c2) * (SHIFTED ? 1.0 : L::W[i]);
+            if constexpr (h != 0.0 && L::keep(a, 0)) {
+              if constexpr (up)
+                acc = madd(Real(h), gp[a], acc);
+              else
+                acc = madd(Real(h), gm[a], acc);
+            }
+          });
+          emit(I, acc);
+        }
+      });
+    }
+  });
+}
+
 // ---------------------------------------------------------------------------
 // Reference state.  Moments are accumulated from the deviations
 // d_i = f_i - w_i rho_ref of the populations from the rest equilibrium
@@ -232,9 +283,14 @@ __host__ __device__ constexpr double kappa(int a, int b) {
 // (Sec. II.E allows finite differences in place of the projection):
 //   a1^(2)_ab = -tau rho cs^2 theta (d_a u_b + d_b u_a - delta_ab div u) (thermal, D = 2), -tau rho cs^2 S
 //   (isothermal); mu cs^2 d_g theta = tau_3 rho cs^4 theta d_g theta in place of Eq. TempGradLBM.
-template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real, bool CLOSURE = false, bool FD = false>
+// KeepInQ: the post-collision populations go back into q.  Any other Out is called as out(I, value) for each
+// population as soon as it is rebuilt, one row pair at a time (rebuild_rows: a caller that stores it at once
+// keeps fewer values live).
+struct KeepInQ {};
+template <class L, int COLL, bool THERMAL, bool SHIFTED, class Real, bool CLOSURE = false, bool FD = false,
+          class Out = KeepInQ>
 __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>& P, const Real* da = nullptr,
-                                        const Real* grad = nullptr) {
+                                        const Real* grad = nullptr, Out&& out = Out{}) {
   using Sc = typename Scalar<Real>::type;
   static_assert(!(THERMAL && !__is_same(Sc, Real)), "the thermal path computes one cell per thread");
   constexpr double c2 = L::CS2;
@@ -441,23 +497,33 @@ __device__ __forceinline__ void collide(Real (&q)[L::Q], const CollParams<Real>&
   // plain storage: f*_i = w^_i + w_i (...); shifted: q*_i = s (f*_i / w_i - rho0) = (...)
   if constexpr (COLL == COLL_BGK) {
     // f* - ref = (1 - 1/tau)(f - ref) + (f^(0) - ref) / tau  (Sec. III.A)
-    rebuild<L, SHIFTED>(C, [&](auto I, Real acc) {
+    auto emit_bgk = [&](auto I, Real acc) {
       constexpr int i = LBM_CI(I);
       const Real dv = P.om1 * d[i] + acc;
-      if constexpr (SHIFTED)
-        q[i] = dv;
+      const Real v = SHIFTED ? dv : Real(ref_weight<L, Sc>(i)) + dv;
+      if constexpr (std::is_same<std::decay_t<Out>, KeepInQ>::value)
+        q[i] = v;
       else
-        q[i] = Real(ref_weight<L, Sc>(i)) + dv;
-    });
+        out(I, v);
+    };
+    if constexpr (std::is_same<std::decay_t<Out>, KeepInQ>::value)
+      rebuild<L, SHIFTED>(C, emit_bgk);
+    else
+      rebuild_rows<L, SHIFTED>(C, emit_bgk);
   } else {
     // f* = f^(0) + (1 - 1/tau) f^(1)  (Eq. RegularizedCollision)
-    rebuild<L, SHIFTED>(C, [&](auto I, Real acc) {
+    auto emit = [&](auto I, Real acc) {
       constexpr int i = LBM_CI(I);
-      if constexpr (SHIFTED)
-        q[i] = acc;
+      const Real v = SHIFTED ? acc : Real(ref_weight<L, Sc>(i)) + acc;
+      if constexpr (std::is_same<std::decay_t<Out>, KeepInQ>::value)
+        q[i] = v;
       else
-        q[i] = Real(ref_weight<L, Sc>(i)) + acc;
-    });
+        out(I, v);
+    };
+    if constexpr (std::is_same<std::decay_t<Out>, KeepInQ>::value)
+      rebuild<L, SHIFTED>(C, emit);
+    else
+      rebuild_rows<L, SHIFTED>(C, emit);
   }
 }
 
