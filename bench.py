@@ -430,8 +430,6 @@ def d3_bench(stream_t, steps=20, n=256, storages=("f32", "f16"), only=None):
         nu = u0 * nx / (2 * np.pi) / 1600.0
         res = {"hermite_order": neq}
         for storage in storages:
-            if storage != "f32" and name == "D3Q103":
-                continue
             p = lbm.make_params3(name, nx, ny, nz, nu=nu, collision="rr", hermite_order=neq, storage=storage,
                                  stream=stream_t.cuda_stream)
             ctx = lbm.lbm3_create(p)

@@ -40,8 +40,7 @@ typedef struct {
   int nx, ny, nz;    /* >= 1 */
   double nu, tau;    /* exactly one > 0: tau is tau-bar of the discrete scheme, nu = cs^2 (tau - 1/2) */
   int bc_x, bc_y, bc_z; /* LBM_PERIODIC or LBM_ZERO_GRADIENT (clamped pull source) */
-  int storage;       /* LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT, LBM_I16_SHIFT (the 16-bit
-                        formats not on D3Q103: LBM_EINVAL) */
+  int storage;       /* LBM_F64, LBM_F32, LBM_F16_SHIFT, LBM_BF16_SHIFT, LBM_I16_SHIFT */
   int compute;       /* LBM_F64 (with LBM_F64 storage) or LBM_F32 (any other storage) */
   double rho0;       /* shifted storage reference density; 0 = 1 */
   double store_scale;/* shifted storage scale s, a power of two; 0 = 1 */

@@ -43,11 +43,12 @@ struct Staged3Blocks {
   static constexpr int MIN = L::Q > 20 ? (sizeof(S) == 2 ? 4 : 3) : 4;
 };
 
-// Storage formats built per lattice: all five, except D3Q103 (FP64 and FP32 only: its kernels are large
-// and each format multiplies the build time).
+// Storage formats: all five on every lattice.  D3Q103's kernels are the largest, so its 16-bit step kernels
+// are built in translation units of their own (d3_q103_<collision>16.cu), compiled in parallel with the
+// FP64 / FP32 ones.
 template <class L>
 struct Storages3 {
-  static constexpr bool SIXTEEN_BIT = L::Q < 100;
+  static constexpr bool SIXTEEN_BIT = true;
 };
 
 // Rows of the direct kernel: interior rows (at least VMAX away from the y and z faces, nx >= VMAX) and the
@@ -371,17 +372,19 @@ inline cudaError_t launch_step3_t(const void* fin, void* fout, const Geom3& g, c
     off.src[i] = off.dst[i] -
                  ((long long)L::CZ[i] * g.plane + (long long)L::CY[i] * g.pitch + L::CX[i]) * (long long)sizeof(S);
   }
-  if (Stage3<L, S>::ENABLED && g.bc[0] == BC_PERIODIC && g.nx % Stage3<L, S>::UNIT == 0 &&
-      g.nx >= Stage3<L, S>::PAD && g.status != nullptr) {
-    const int nbt = (g.nx + Stage3<L, S>::BXT - 1) / Stage3<L, S>::BXT;
-    const long long ntiles = (long long)nbt * g.ny * g.nz;
-    int grid = 0;
-    const int e = staged_grid<L, COLL, Real, S>(&grid);
-    if (e) return (cudaError_t)e;
-    const long long nb = ntiles < grid ? ntiles : grid;
-    k_step3_staged<L, COLL, Real, S><<<(unsigned)nb, Stage3<L, S>::THREADS, Stage3<L, S>::SMEM, st>>>(
-        (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<Real>(pd), off);
-    return cudaGetLastError();
+  if constexpr (Stage3<L, S>::ENABLED) {  // (not instantiated at all where disabled: D3Q103)
+    if (g.bc[0] == BC_PERIODIC && g.nx % Stage3<L, S>::UNIT == 0 && g.nx >= Stage3<L, S>::PAD &&
+        g.status != nullptr) {
+      const int nbt = (g.nx + Stage3<L, S>::BXT - 1) / Stage3<L, S>::BXT;
+      const long long ntiles = (long long)nbt * g.ny * g.nz;
+      int grid = 0;
+      const int e = staged_grid<L, COLL, Real, S>(&grid);
+      if (e) return (cudaError_t)e;
+      const long long nb = ntiles < grid ? ntiles : grid;
+      k_step3_staged<L, COLL, Real, S><<<(unsigned)nb, Stage3<L, S>::THREADS, Stage3<L, S>::SMEM, st>>>(
+          (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<Real>(pd), off);
+      return cudaGetLastError();
+    }
   }
   const int nbx = (g.nx + STEP_BX - 1) / STEP_BX;
   const Rows3 rows = rows3<L::VMAX>(g);
@@ -403,20 +406,31 @@ inline cudaError_t launch_step3_t(const void* fin, void* fout, const Geom3& g, c
 }
 
 template <class L, int COLL>
-inline cudaError_t launch_step3_prec(int prec, const void* fin, void* fout, const Geom3& g, const CollParamsD& pd,
-                                     cudaStream_t st) {
+inline cudaError_t launch_step3_prec_wide(int prec, const void* fin, void* fout, const Geom3& g,
+                                          const CollParamsD& pd, cudaStream_t st) {
   switch (prec) {
     case PREC_F64: return launch_step3_t<L, COLL, double, double>(fin, fout, g, pd, st);
     case PREC_F32: return launch_step3_t<L, COLL, float, float>(fin, fout, g, pd, st);
   }
-  if constexpr (Storages3<L>::SIXTEEN_BIT) {
-    switch (prec) {
-      case PREC_F16: return launch_step3_t<L, COLL, float, __half>(fin, fout, g, pd, st);
-      case PREC_BF16: return launch_step3_t<L, COLL, float, __nv_bfloat16>(fin, fout, g, pd, st);
-      case PREC_I16: return launch_step3_t<L, COLL, float, short>(fin, fout, g, pd, st);
-    }
+  return cudaErrorInvalidValue;
+}
+
+template <class L, int COLL>
+inline cudaError_t launch_step3_prec_16(int prec, const void* fin, void* fout, const Geom3& g, const CollParamsD& pd,
+                                        cudaStream_t st) {
+  switch (prec) {
+    case PREC_F16: return launch_step3_t<L, COLL, float, __half>(fin, fout, g, pd, st);
+    case PREC_BF16: return launch_step3_t<L, COLL, float, __nv_bfloat16>(fin, fout, g, pd, st);
+    case PREC_I16: return launch_step3_t<L, COLL, float, short>(fin, fout, g, pd, st);
   }
   return cudaErrorInvalidValue;
+}
+
+template <class L, int COLL>
+inline cudaError_t launch_step3_prec(int prec, const void* fin, void* fout, const Geom3& g, const CollParamsD& pd,
+                                     cudaStream_t st) {
+  if (prec == PREC_F64 || prec == PREC_F32) return launch_step3_prec_wide<L, COLL>(prec, fin, fout, g, pd, st);
+  return launch_step3_prec_16<L, COLL>(prec, fin, fout, g, pd, st);
 }
 
 // Step launchers of one (lattice, collision) pair: one translation unit each, so that the 3D kernels

@@ -119,7 +119,7 @@ def test_3d_lattice_info_matches_oracle(lbm, name):
 def test_3d_invalid_parameters_are_rejected_on_host(lbm):
     bad = [dict(lattice="D3Q19", hermite_order=4), dict(lattice="D3Q27", reg_order=7),
            dict(lattice="D3Q19", tau=0.5), dict(lattice="D3Q19", nz=0), dict(lattice="D3Q19", bc=(0, 0, 3)),
-           dict(lattice="D3Q103", storage="bf16"), dict(lattice=42)]
+           dict(lattice="D3Q103", storage=9), dict(lattice=42)]
     for kw in bad:
         kw.setdefault("tau", 0.8)
         with pytest.raises(lbm.LbmError) as e:

@@ -135,7 +135,7 @@ def test_init_and_moments_match_oracle(name, storage):
 
 @pytest.mark.parametrize("nx", [140, 144])  # 140: rows not whole 16-byte units (direct loads); 144: staged
 @pytest.mark.parametrize("storage,tol", [("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
-@pytest.mark.parametrize("name", ["D3Q19", "D3Q27", "D3V39"])
+@pytest.mark.parametrize("name", ["D3Q19", "D3Q27", "D3V39", "D3Q103"])
 def test_shifted_16bit_storage(name, storage, tol, nx):
     nz, ny, _ = shape_for(name)
     f = random_state(name, (nz, ny, nx), 5)
