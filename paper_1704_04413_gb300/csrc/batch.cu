@@ -36,7 +36,10 @@ struct BatchInst {
   const void* fin;
   void* fout;
   StepGeom g;
-  CollParams<F2> P;
+  union {
+    CollParams<F2> P;      // D2Q9 / D2V17: two cells a thread
+    CollParams<float> Pf;  // D2V37: one cell a thread, read in place from the constant bank
+  };
   int ntx;         // items per row band
   int lattice;     // LBM_D2Q9, LBM_D2V17 or LBM_D2V37
   long long item0; // first work item of the instance
@@ -48,6 +51,7 @@ struct BatchDesc {
   long long total;  // work items of all instances
   BatchInst inst[kBatchMax];
 };
+static_assert(sizeof(BatchDesc) <= 32764, "the instance table travels as one kernel parameter");
 
 // The rows of one work item of instance I on lattice L.
 template <class L, int COLL, class S>
@@ -68,22 +72,10 @@ __device__ __forceinline__ void batch_item_v37(const BatchInst& I, int rows, int
   const S* fin = static_cast<const S*>(I.fin);
   S* fout = static_cast<S*>(I.fout);
   const GeomOffsets<D2V37, S> off{I.g.plane * (long long)sizeof(S), (long long)I.g.pitch * (long long)sizeof(S)};
-  CollParams<float> P;  // both lanes of the pair parameters hold the same values
-  P.omega = I.P.omega.v.x;
-  P.om1 = I.P.om1.v.x;
-  P.om1_3 = I.P.om1_3.v.x;
-  P.om1_4 = I.P.om1_4.v.x;
-  P.tau = I.P.tau.v.x;
-  P.tau3 = I.P.tau3.v.x;
-  P.neq = I.P.neq;
-  P.nreg = I.P.nreg;
-  P.rho0 = I.P.rho0.v.x;
-  P.s = I.P.s.v.x;
-  P.inv_s = I.P.inv_s.v.x;
   for (int r = 0; r < rows; ++r) {
     const int y = band * rows + r;
     if (y >= I.g.ny) break;
-    step_cell<D2V37, COLL, false, float, S, false>(fin, fout, I.g, P, off, nullptr, x, y);
+    step_cell<D2V37, COLL, false, float, S, false>(fin, fout, I.g, I.Pf, off, nullptr, x, y);
   }
 }
 
@@ -190,7 +182,18 @@ BatchDesc make_desc(const lbm_batch* b, int flip) {
       I.fin = c->buf[cur];
       I.fout = c->buf[cur ^ 1];
       I.g = c->g;
-      I.P = cast_params<F2>(lbm_ctx_coll_params(c));
+      const CollParamsD pd = lbm_ctx_coll_params(c);
+      const double s_store = c->prec >= PREC_F16 ? pd.s : 1.0;  // the shifted 16-bit formats
+      if (lattice == LBM_D2V37) {
+        I.Pf = cast_params<float>(pd);
+        set_coef_factors<D2V37>(I.Pf, c->p.collision, pd.neq, pd.nreg, pd.omega, pd.om1, pd.om1_3, pd.om1_4, s_store);
+      } else {
+        I.P = cast_params<F2>(pd);
+        if (lattice == LBM_D2V17)
+          set_coef_factors<D2V17>(I.P, c->p.collision, pd.neq, pd.nreg, pd.omega, pd.om1, pd.om1_3, pd.om1_4, s_store);
+        else
+          set_coef_factors<D2Q9>(I.P, c->p.collision, pd.neq, pd.nreg, pd.omega, pd.om1, pd.om1_3, pd.om1_4, s_store);
+      }
       const int cells = lattice == LBM_D2V37 ? b->threads : 2 * b->threads;  // columns of an item
       I.ntx = (c->p.nx + cells - 1) / cells;
       I.lattice = lattice;

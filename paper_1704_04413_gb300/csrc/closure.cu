@@ -765,7 +765,10 @@ static bool closure_ctx_ok(const lbm_ctx* c) {
 }
 
 static lbm::CollParams<float> closure_coll_params(const lbm_ctx* c) {
-  return lbm::cast_params<float>(lbm_ctx_coll_params(c));
+  const lbm::CollParamsD pd = lbm_ctx_coll_params(c);
+  lbm::CollParams<float> P = lbm::cast_params<float>(pd);
+  lbm::set_coef_factors<lbm::D2Q9>(P, lbm::COLL_RR, pd.neq, pd.nreg, pd.omega, pd.om1, pd.om1_3, pd.om1_4, 1.0);
+  return P;
 }
 
 int lbm_closure_apply(lbm_ctx* c, const float* y, double u0) {

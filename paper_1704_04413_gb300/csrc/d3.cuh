@@ -165,6 +165,73 @@ __global__ void __launch_bounds__(STEP_BX, Step3Blocks<L, Real>::MIN)
   });
 }
 
+// Two cells a thread for the interior rows of D3Q103 with the RR collision, on x-periodic grids of even nx:
+// thread t of a block takes columns x = 2 t, 2 t + 1 of its row and collides both in packed FP32x2
+// (vec2.cuh), one instruction for both cells, which halves the instructions fetched per cell of this
+// lattice's long, fully unrolled collision (the one-cell kernel is bound by instruction fetch).  The
+// collision runs as a stream (collide3_rr): each pulled population pair enters the moments as it arrives and
+// each rebuilt pair is stored at once, so neither the 103 pulled nor the 103 rebuilt pairs stay live.  An
+// even x-velocity is pulled with one aligned load for both cells, an odd one with one load a cell; each
+// store is one aligned pair.
+// Four 128-thread blocks a SM (128 registers, no spills): measured at 256^3 (FP32 / binary16 GLUPS) against
+// 5.29 / 6.49 at two blocks, 6.15 / 7.26 at three and 5.92 / 7.34 at five (88 B of spills); the one-cell
+// kernel ran 5.70 / 6.64.
+template <class L, class S>
+struct Step3Pair {
+  static constexpr bool ENABLED = L::Q > 100;
+  static constexpr int MIN_BLOCKS = 4;
+};
+
+template <class L, class S>
+__global__ void __launch_bounds__(STEP_BX, Step3Pair<L, S>::MIN_BLOCKS)
+    k_step3_pair(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, Rows3 rows, CollParams<F2> P,
+                 const __grid_constant__ PullOffsets3<L::Q> off) {
+  const int rb = blockIdx.x / nbx;
+  const int bx = blockIdx.x - rb * nbx;
+  const int z = L::VMAX + rb / rows.ny_in;
+  const int y = L::VMAX + (rb - (rb / rows.ny_in) * rows.ny_in);
+  const int x_raw = 2 * (bx * STEP_BX + (int)threadIdx.x);
+  const bool act = x_raw < g.nx;  // nx is even: a pair is whole or absent
+  const int x = act ? x_raw : g.nx - 2;
+  const long long cen = (long long)z * g.plane + (long long)y * g.pitch + x;
+  const char* c = reinterpret_cast<const char*>(fin + cen);
+  // one base pointer per x-velocity and cell, moved by a whole row where x - c_x leaves [0, nx) (periodic x,
+  // nx >= VMAX: one fold); an even c_x moves both cells of the pair together
+  const char* cb0[2 * L::VMAX + 1];
+  const char* cb1[2 * L::VMAX + 1];
+  auto fold = [&](int xs) { return (xs < 0 ? g.nx : 0) - (xs >= g.nx ? g.nx : 0); };
+  sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+    constexpr int j = LBM_CI(J);
+    constexpr int cx = j - L::VMAX;
+    if constexpr (cx == 0) {
+      cb0[j] = c;
+      cb1[j] = c;
+    } else {
+      cb0[j] = c + (long long)fold(x - cx) * (long long)sizeof(S);
+      cb1[j] = (cx % 2 == 0) ? cb0[j] : c + (long long)fold(x + 1 - cx) * (long long)sizeof(S);
+    }
+  });
+  char* o = reinterpret_cast<char*>(fout + cen);
+  collide3_rr<L, Store<S>::SHIFTED, F2>(
+      [&](auto I) -> F2 {
+        constexpr int i = LBM_CI(I);
+        constexpr int j = L::CX[i] + L::VMAX;
+        const long long so = off.src[i];
+        if constexpr (L::CX[i] % 2 == 0) {
+          return ld_pair<S>(cb0[j] + so);
+        } else {
+          const float a = ld_raw<S>(cb0[j] + so);
+          const float b = ld_raw<S>(cb1[j] + so + (long long)sizeof(S));
+          return F2(a, b);
+        }
+      },
+      P,
+      [&](auto I, F2 v) {
+        constexpr int i = LBM_CI(I);
+        if (act) st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), v);
+      });
+}
+
 // Staged variant for x-periodic grids whose rows are whole 16-byte units: a persistent block walks row tiles
 // of BXT cells (256, or 128 where a 256-cell stage would exceed 44 KB).  A producer warp copies every
 // population's source row segment of a tile, pull-shifted in y and z, with cp.async.bulk into a ring of
@@ -403,8 +470,21 @@ inline cudaError_t launch_step3_t(const void* fin, void* fout, const Geom3& g, c
   }
   const long long nb_in = (long long)nbx * rows.interior, nb_edge = (long long)nbx * rows.edge;
   if (nb_in > 0x7fffffffLL || nb_edge > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_step3<L, COLL, Real, S, ROWS_INTERIOR><<<(unsigned)nb_in, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
-                                                                                rows, P, off);
+  bool pairs = false;
+  if constexpr (Step3Pair<L, S>::ENABLED && COLL == COLL_RR && sizeof(Real) == 4)
+    pairs = g.bc[0] == BC_PERIODIC && g.nx % 2 == 0 && g.nx >= L::VMAX;
+  if (pairs) {
+    if constexpr (Step3Pair<L, S>::ENABLED && COLL == COLL_RR && sizeof(Real) == 4) {
+      const int nbx2 = (g.nx + 2 * STEP_BX - 1) / (2 * STEP_BX);
+      const long long nb2 = (long long)nbx2 * rows.interior;
+      if (nb2 > 0x7fffffffLL) return cudaErrorInvalidValue;
+      k_step3_pair<L, S><<<(unsigned)nb2, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx2, rows,
+                                                           cast_params<F2>(pd), off);
+    }
+  } else {
+    k_step3<L, COLL, Real, S, ROWS_INTERIOR><<<(unsigned)nb_in, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
+                                                                                  rows, P, off);
+  }
   k_step3<L, COLL, Real, S, ROWS_EDGE><<<(unsigned)nb_edge, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, rows,
                                                                             P, off);
   return cudaGetLastError();

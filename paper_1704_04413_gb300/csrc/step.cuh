@@ -54,6 +54,15 @@ __host__ __device__ inline CollParams<Real> cast_params(const CollParamsD& d) {
   return p;
 }
 
+// Parameters of a 2D collision on lattice L with storage S (coll: COLL_*), with the per-coefficient factors
+// of the rebuild (plain storage has no scale).
+template <class L, class Real, class S>
+inline CollParams<Real> coll_params_2d(const CollParamsD& d, int coll) {
+  CollParams<Real> p = cast_params<Real>(d);
+  set_coef_factors<L>(p, coll, d.neq, d.nreg, d.omega, d.om1, d.om1_3, d.om1_4, Store<S>::SHIFTED ? d.s : 1.0);
+  return p;
+}
+
 __device__ __forceinline__ int src_coord(int x, int c, int n, int bc) {
   int s = x - c;
   if (bc == BC_PERIODIC) {
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(STEP_BX, StepBlocks<L, THERMAL, Real>::MIN)
 #define LBM_STEP_STAGED 1
 #endif
 #ifndef LBM_STEP2_MINB_LARGE_F16
-#define LBM_STEP2_MINB_LARGE_F16 5
+#define LBM_STEP2_MINB_LARGE_F16 4
 #endif
 #ifndef LBM_STEP_PAIRS_LARGE_16
 #define LBM_STEP_PAIRS_LARGE_16 1
@@ -312,9 +321,9 @@ __device__ __forceinline__ void st_pair<__nv_bfloat16>(__nv_bfloat16* p, F2 v) {
   *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.v.x, v.v.y);
 }
 
-// Blocks per SM of the pair kernel.  D2V37 with binary16 storage runs at 96 registers (five blocks, 24-28 B
-// of spills; 31.7 -> 35.3 GLUPS at 4096^2): its conversions gain from the extra warps, while the bfloat16
-// kernel (36.5 -> 35.0) and the others keep their unbounded allocation.
+// Blocks per SM of the pair kernel.  D2V37 with binary16 storage is held to four blocks (128 registers; it
+// takes 122): at five (96 registers) its 44 B of spills cost 35.7 -> 30.6 GLUPS at 4096^2.  The others keep
+// their unbounded allocation (bfloat16 D2V37: 126 registers).
 template <class L, class S>
 struct Step2Blocks {
   static constexpr int MIN =
@@ -697,16 +706,16 @@ inline cudaError_t launch_step2_t(const void* fin, void* fout, const StepGeom& g
       const long long nb = ntiles < grid ? ntiles : grid;
       if (nbt == 1)
         k_step2_staged<L, COLL, S, ROWS_WHOLE><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
-            (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+            (const S*)fin, (S*)fout, g, nbt, ntiles, coll_params_2d<L, F2, S>(pd, COLL), off, *ctl);
       else
         k_step2_staged<L, COLL, S, ROWS_MARGIN><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
-            (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+            (const S*)fin, (S*)fout, g, nbt, ntiles, coll_params_2d<L, F2, S>(pd, COLL), off, *ctl);
     } else {
       const int e = staged2_grid<L, COLL, S, ROWS_ANY>(&grid);
       if (e) return (cudaError_t)e;
       const long long nb = ntiles < grid ? ntiles : grid;
       k_step2_staged<L, COLL, S, ROWS_ANY><<<(unsigned)nb, St::THREADS, St::SMEM, st>>>(
-          (const S*)fin, (S*)fout, g, nbt, ntiles, cast_params<F2>(pd), off, *ctl);
+          (const S*)fin, (S*)fout, g, nbt, ntiles, coll_params_2d<L, F2, S>(pd, COLL), off, *ctl);
     }
     return cudaGetLastError();
     }
@@ -715,7 +724,7 @@ inline cudaError_t launch_step2_t(const void* fin, void* fout, const StepGeom& g
   const long long nblocks = (long long)nbx * g.ny;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_step2<L, COLL, S><<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
-                                                                 cast_params<F2>(pd), off);
+                                                                 coll_params_2d<L, F2, S>(pd, COLL), off);
   return cudaGetLastError();
 }
 
@@ -731,7 +740,8 @@ inline cudaError_t launch_step_t(const void* fin, void* fout, const StepGeom& g,
   const long long nblocks = (long long)nbx * g.ny;
   if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_step<L, COLL, THERMAL, Real, S>
-      <<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, cast_params<Real>(pd), off);
+      <<<(unsigned)nblocks, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, coll_params_2d<L, Real, S>(pd, COLL),
+                                              off);
   return cudaGetLastError();
 }
 
@@ -764,7 +774,7 @@ template <class L, bool THERMAL, class Real, class S>
 inline cudaError_t launch_step_fd_t(const void* fin, void* fout, const StepGeom& g, const CollParamsD& pd,
                                     void* mom, cudaStream_t st) {
   const long long n = (long long)g.nx * g.ny;
-  const CollParams<Real> P = cast_params<Real>(pd);
+  const CollParams<Real> P = coll_params_2d<L, Real, S>(pd, COLL_RR);
   k_stream_moments<L, THERMAL, Real, S><<<(unsigned)((n + 127) / 128), 128, 0, st>>>((const S*)fin, g, P,
                                                                                      (Real*)mom);
   PullOffsets<L::Q> off;

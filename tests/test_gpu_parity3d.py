@@ -230,3 +230,38 @@ def test_staged_ring_reuse(storage):
         c.m.lbm3_step(c.ctx, 2)
         got = c.get_oracle_f()
     assert pop_rel(got, ref, o.lattice(name).w) <= 2 * TOL[storage]
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", 2e-6), ("f16", 2e-3), ("bf16", 2e-2), ("i16", 2e-3)])
+def test_d3q103_pair_kernel_interior_rows(storage, tol):
+    """A grid whose edge rows (within 3 of a y or z face) are at most an eighth of its rows runs the interior
+    rows in their own launch, which for D3Q103 RR on an x-periodic grid of even nx is the two-cell kernel:
+    one step against the oracle's collision of the stored populations, on every cell of sampled interior and
+    edge rows.  FP32 at D3Q103's per-collision bound; 16-bit formats within a fraction of the deviation scale
+    they resolve (their output is rounded to the format)."""
+    name = "D3Q103"
+    nz, ny, nx = 94, 94, 36  # 8 x 1092 edge rows <= 94^2: split; 18 pairs a row, the x wrap at both ends
+    f = random_state(name, (nz, ny, nx), 13)
+    with Ctx3(name, nx, ny, nz, 0.62, "rr", 2, 0, storage) as c:
+        c.set_oracle_f(f)
+        pre = c.get_oracle_f()
+        c.m.lbm3_step(c.ctx, 1)
+        got = c.get_oracle_f()
+    L = o.lattice(name)
+    zs = np.array([0, 2, 3, 4, 47, 89, 90, 91, 93])
+    Z, Y, X = np.meshgrid(zs, zs, np.arange(nx), indexing="ij")
+    Z, Y, X = Z.ravel(), Y.ravel(), X.ravel()
+    fs = np.empty((L.V, Z.size))
+    for i in range(L.V):
+        cx, cy, cz = (int(v) for v in L.xi[i])
+        fs[i] = pre[i, (Z - cz) % nz, (Y - cy) % ny, (X - cx) % nx]
+    p = o.Params3(name, nx, ny, nz, 0.62, "rr", hermite_order=2)
+    ref = o.collide(p, fs)
+    out = got[:, Z, Y, X]
+    if storage == "f32":
+        e_pop, e_big = coll_errors(out, ref, L.w)
+        assert e_pop <= tol, "pop_rel %.3e max_rel(|f| >= w/10) %.3e" % (e_pop, e_big)
+    else:
+        w = L.w[:, None]
+        dev = np.abs(ref / w - 1.0).max()
+        assert np.max(np.abs(out - ref) / w) <= tol * dev
