@@ -212,6 +212,55 @@ __host__ __device__ constexpr int first_pop3(int k, int l, int m) {
   return -1;
 }
 
+// Monomial moments of order <= 2, D[k][l][m] = sum_i cx^k cy^l cz^m d_i: summed directly over the
+// populations, or in two stages over the velocity set grouped by (cy, cz),
+//   R_k(y, z) = sum_{i: (cy_i, cz_i) = (y, z)} cx_i^k d_i,   D[k][l][m] = sum_(y, z) y^l z^m R_k(y, z),
+// where that saves a fifth of the multiply-adds or more (D3Q27 130 against 171, D3Q103 570 against 751).
+template <class L>
+__host__ __device__ constexpr int moments_cost_direct() {
+  int n = 0;
+  for (int k = 0; k <= 2; ++k)
+    for (int l = 0; l + k <= 2; ++l)
+      for (int m = 0; m + l + k <= 2; ++m)
+        if (needs_monomial<L>(k, l, m, 2))
+          for (int i = 0; i < L::Q; ++i)
+            if (ipow(L::CX[i], k) * ipow(L::CY[i], l) * ipow(L::CZ[i], m) != 0.0) ++n;
+  return n;
+}
+// Whether the group (y, z) has a member with cx^k != 0, and the first such member (-1: none).
+template <class L>
+__host__ __device__ constexpr int group_first_k(int y, int z, int k) {
+  for (int j = 0; j < count_yz<L>(y, z); ++j)
+    if (ipow(L::CX[member_yz<L>(y, z, j)], k) != 0.0) return j;
+  return -1;
+}
+template <class L>
+__host__ __device__ constexpr int moments_cost_grouped() {
+  int n = 0;
+  for (int z = -L::VMAX; z <= L::VMAX; ++z)
+    for (int y = -L::VMAX; y <= L::VMAX; ++y) {
+      if (count_yz<L>(y, z) == 0) continue;
+      for (int k = 0; k <= 2; ++k) {
+        for (int j = 0; j < count_yz<L>(y, z); ++j)
+          if (ipow(L::CX[member_yz<L>(y, z, j)], k) != 0.0) ++n;
+        if (group_first_k<L>(y, z, k) < 0) continue;
+        for (int l = 0; l + k <= 2; ++l)
+          for (int m = 0; m + l + k <= 2; ++m)
+            if (needs_monomial<L>(k, l, m, 2) && ipow(y, l) * ipow(z, m) != 0.0) ++n;
+      }
+    }
+  return n;
+}
+// First group (as (z + VMAX) (2 VMAX + 1) + y + VMAX) with a term in D[k][l][m] (-1: none).
+template <class L>
+__host__ __device__ constexpr int first_group(int k, int l, int m) {
+  for (int z = -L::VMAX; z <= L::VMAX; ++z)
+    for (int y = -L::VMAX; y <= L::VMAX; ++y)
+      if (count_yz<L>(y, z) > 0 && group_first_k<L>(y, z, k) >= 0 && ipow(y, l) * ipow(z, m) != 0.0)
+        return (z + L::VMAX) * (2 * L::VMAX + 1) + y + L::VMAX;
+  return -1;
+}
+
 // The RR collision (projected a1^(2), Eq. MalaspinasRecursiveRelation in the closed form above) of one cell,
 // or of two cells in packed FP32x2, as a stream: ld(I) gives the pulled population i (storage representation
 // as Real), and the monomial moments take it as it arrives, so that no population has to stay live through
@@ -224,6 +273,44 @@ __device__ __forceinline__ void collide3_rr(Ld&& ld, const CollParams<Real>& P, 
 
   // monomial moments of order <= 2 of the deviations d_i (Sec. II.A), D[k][l][m] = sum_i d_i cx^k cy^l cz^m
   Real D[3][3][3];
+  if constexpr (5 * moments_cost_grouped<L>() <= 4 * moments_cost_direct<L>()) {
+    sfor<0, 2 * L::VMAX + 1>([&](auto Zi) {
+      constexpr int zv = LBM_CI(Zi) - L::VMAX;
+      sfor<0, 2 * L::VMAX + 1>([&](auto Yi) {
+        constexpr int yv = LBM_CI(Yi) - L::VMAX;
+        constexpr int gid = LBM_CI(Zi) * (2 * L::VMAX + 1) + LBM_CI(Yi);
+        if constexpr (count_yz<L>(yv, zv) > 0) {
+          Real R[3];
+          sfor<0, count_yz<L>(yv, zv)>([&](auto J) {
+            constexpr int j = LBM_CI(J);
+            constexpr int i = member_yz<L>(yv, zv, j);
+            [[maybe_unused]] constexpr double wr = (double)(Sc)L::W[i];
+            Real di = ld(IC<i>{});
+            if constexpr (!SHIFTED) di = di - Real(wr);
+            sfor<0, 3>([&](auto K) {
+              constexpr int k = LBM_CI(K);
+              constexpr double c = ipow(L::CX[i], k) * (SHIFTED ? L::W[i] : 1.0);
+              if constexpr (c != 0.0) add_term<j == group_first_k<L>(yv, zv, k)>(R[k], c, di);
+            });
+          });
+          sfor<0, 3>([&](auto K) {
+            constexpr int k = LBM_CI(K);
+            if constexpr (group_first_k<L>(yv, zv, k) >= 0) {
+              sfor<0, 3 - k>([&](auto Lq) {
+                constexpr int l = LBM_CI(Lq);
+                sfor<0, 3 - k - l>([&](auto M) {
+                  constexpr int m = LBM_CI(M);
+                  constexpr double h = ipow(yv, l) * ipow(zv, m);
+                  if constexpr (needs_monomial<L>(k, l, m, 2) && h != 0.0)
+                    add_term<gid == first_group<L>(k, l, m)>(D[k][l][m], h, R[k]);
+                });
+              });
+            }
+          });
+        }
+      });
+    });
+  } else {
   sfor<0, L::Q>([&](auto I) {
     constexpr int i = LBM_CI(I);
     [[maybe_unused]] constexpr double wr = (double)(Sc)L::W[i];
@@ -244,6 +331,7 @@ __device__ __forceinline__ void collide3_rr(Ld&& ld, const CollParams<Real>& P, 
       });
     });
   });
+  }
   if constexpr (SHIFTED) {
     sfor<0, 3>([&](auto K) {
       constexpr int k = LBM_CI(K);

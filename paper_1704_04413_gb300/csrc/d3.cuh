@@ -190,9 +190,8 @@ __global__ void __launch_bounds__(STEP_BX, Step3Pair<L, S>::MIN_BLOCKS)
   const int bx = blockIdx.x - rb * nbx;
   const int z = L::VMAX + rb / rows.ny_in;
   const int y = L::VMAX + (rb - (rb / rows.ny_in) * rows.ny_in);
-  const int x_raw = 2 * (bx * STEP_BX + (int)threadIdx.x);
-  const bool act = x_raw < g.nx;  // nx is even: a pair is whole or absent
-  const int x = act ? x_raw : g.nx - 2;
+  const int x = 2 * (bx * STEP_BX + (int)threadIdx.x);
+  if (x >= g.nx) return;  // nx is even: a pair is whole or absent (no barrier below)
   const long long cen = (long long)z * g.plane + (long long)y * g.pitch + x;
   const char* c = reinterpret_cast<const char*>(fin + cen);
   // one base pointer per x-velocity and cell, moved by a whole row where x - c_x leaves [0, nx) (periodic x,
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(STEP_BX, Step3Pair<L, S>::MIN_BLOCKS)
       P,
       [&](auto I, F2 v) {
         constexpr int i = LBM_CI(I);
-        if (act) st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), v);
+        st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), v);
       });
 }
 
