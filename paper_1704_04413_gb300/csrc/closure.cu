@@ -3,10 +3,11 @@
 // predicting the subgrid stress <rho u_a u_b> - rho_bar u_bar_a u_bar_b that box filtering of a
 // fine run leaves out of the coarse equilibrium, which the coarse RR step adds to its a1^(2).
 //
-// Every matrix product runs on the tensor cores as BF16 x BF16 -> FP32 warp MMAs
-// (mma.sync m16n8k16): inference chains the layers through registers (the FP32 accumulator
-// fragment of one layer is, after bias + GELU and rounding to BF16, the A fragment of the next);
-// training keeps each layer's activations in shared memory and forms the weight gradients
+// Every matrix product runs on the tensor cores, BF16 x BF16 -> FP32.  Inference (lbm_closure_forward and
+// the fused closure step) runs on the 5th-generation tensor core: per 128-row tile each layer is a chain of
+// tcgen05 MMAs into a TMEM accumulator (tc.cuh), whose rows the block's threads read back, activate, round
+// to BF16 and store as the next layer's shared-memory operand.  Training uses warp MMAs
+// (mma.sync m16n8k16): it keeps each layer's activations in shared memory and forms the weight gradients
 // (activation^T x upstream gradient) and the input gradients (upstream gradient x weights) with
 // the same MMA, accumulating per-block partial gradients into FP32 with atomics; Adam updates
 // FP32 master weights and refreshes their BF16 copies.
@@ -19,12 +20,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstddef>
 #include <cstring>
 #include <new>
 
 #include "../../include/lbm.h"
 #include "ctx.h"
 #include "fields.h"
+#include "tc.cuh"
+#include "vec2.cuh"
 
 namespace {
 
@@ -60,6 +64,17 @@ __device__ __forceinline__ float gelu_grad(float z) {
   const float u = k * (z + 0.044715f * z * z * z);
   const float t = tanh_hw(u);
   return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k * (1.0f + 3.0f * 0.044715f * z * z);
+}
+
+// GELU of two values in packed FP32x2 (the same tanh form; per lane the operations of gelu() written out as
+// z^2, 1 + c z^2, (k z)(...), then 0.5 z + 0.5 z tanh), for the tensor-core epilogue.
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  const float2 z2 = __fmul2_rn(z, z);
+  const float2 t = __ffma2_rn(make_float2(0.044715f, 0.044715f), z2, make_float2(1.0f, 1.0f));
+  const float2 u = __fmul2_rn(__fmul2_rn(make_float2(0.7978845608028654f, 0.7978845608028654f), z), t);
+  const float2 th = make_float2(tanh_hw(u.x), tanh_hw(u.y));
+  const float2 hz = __fmul2_rn(make_float2(0.5f, 0.5f), z);
+  return __ffma2_rn(hz, th, hz);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -147,114 +162,219 @@ __device__ void load_weights(SmemWeights& s, const __nv_bfloat16* wb, const floa
   }
 }
 
-// B fragments of a [out][in] weight matrix for the k-chunk k0 and output tile n0 (B[k][n] = W[n][k]).
-__device__ __forceinline__ void wfrag(uint32_t (&rb)[2], const __nv_bfloat16* w, int in_dim, int k0, int n0) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const __nv_bfloat16* row = w + (n0 + g) * in_dim + k0 + 2 * t;
-  rb[0] = *reinterpret_cast<const uint32_t*>(row);
-  rb[1] = *reinterpret_cast<const uint32_t*>(row + 8);
+// ---------------------------------------------------------------------------
+// Inference on the 5th-generation tensor core.  A block runs two independent groups of 128 threads (TC_G), each
+// taking 128 rows at a time with its own operand buffer, TMEM accumulator and mbarrier, so that one group's
+// MMAs run while the other applies its activations; the weights in shared memory serve both.  Each layer is a
+// chain of tcgen05 MMAs (M = 128 rows, N = 64 outputs, or 16 for the output layer, K = 16 a step) issued by one
+// thread of the group into its TMEM accumulator, completing on its mbarrier.  Each thread then loads its row
+// of the accumulator from TMEM, adds the bias, applies GELU, rounds to BF16 and writes the row into the
+// group's shared operand of the next layer.  Operands are in the canonical no-swizzle K-major layout: core
+// matrix (row group g, K chunk c) of 8 rows x 8 BF16 at element ((g * KCH + c) * 64), KCH = K / 8.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128;  // rows of a group's tile, threads of a group
+constexpr int TC_G = 2;    // groups a block
+constexpr int TC_NO = 16;  // output layer padded to the smallest N of an M = 128 MMA
+constexpr int TC_COLS = 128;  // TMEM columns a block: 64 a group
+
+struct __align__(128) SmemTc {
+  __nv_bfloat16 w1[NH * NI];        // 4 KB
+  __nv_bfloat16 w2[NH * NH];        // 8 KB
+  __nv_bfloat16 w3[NH * NH];        // 8 KB
+  __nv_bfloat16 w4[TC_NO * NH];     // 2 KB, rows NO..15 zero
+  __nv_bfloat16 a[TC_G][TC_M * NH]; // 16 KB a group: the current layer's input rows
+  float b1[NH], b2[NH], b3[NH], b4[NO];
+  uint64_t bar[TC_G];
+  uint32_t tmem;
+};
+static_assert(offsetof(SmemTc, a) % 128 == 0 && offsetof(SmemTc, w4) % 128 == 0, "128-byte core matrices");
+
+// Element offset of (row r, column k) in the canonical layout of a matrix with K columns.
+__device__ __forceinline__ int canon(int r, int k, int K) {
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-// Hidden layer on register fragments of two independent 16-row tiles: in a[2][KC][4] (K = 16 KC), out
-// GELU(a W^T + b) as the next layer's A fragments a_next[2][4][4] (K = 64).  Each weight fragment is read
-// once for both tiles and the two MMA chains overlap.
-template <int KC>
-__device__ __forceinline__ void dense_gelu2(const uint32_t (&a)[2][KC][4], const __nv_bfloat16* w, const float* b,
-                                            uint32_t (&a_next)[2][4][4]) {
-  const int lane = threadIdx.x & 31, t = lane & 3;
-  float acc[2][8][4];
+// Barrier of one group (named barrier 1 + g, its 128 threads), and the same with a logical AND of `pred`.
+// (Immediate barrier numbers: a register operand makes the compiler reserve all sixteen.)
+__device__ __forceinline__ void group_sync(int g) {
+  static_assert(TC_G == 2 && TC_M == 128, "barriers 1 and 2 of 128 threads");
+  if (g == 0)
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+  else
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+__device__ __forceinline__ bool group_sync_and(int g, bool pred) {
+  uint32_t out;
+  if (g == 0)
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(out)
+        : "r"((uint32_t)pred)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(out)
+        : "r"((uint32_t)pred)
+        : "memory");
+  return out != 0;
+}
+
+// Bias, GELU and BF16 rounding of this thread's accumulator row (64 TMEM columns from trow), written as row m
+// of the group's next-layer input a.
+__device__ __forceinline__ void tc_hidden_epilogue(__nv_bfloat16* a, uint32_t trow, const float* bias, int m) {
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const float b0 = b[j * 8 + 2 * t], b1 = b[j * 8 + 2 * t + 1];
+  for (int q = 0; q < 4; ++q) {
+    uint32_t r[16];
+    lbm::tc::ld_32x32b_x16(trow + 16 * q, r);
+    lbm::tc::wait_ld();
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      acc[h][j][0] = b0;
-      acc[h][j][1] = b1;
-      acc[h][j][2] = b0;
-      acc[h][j][3] = b1;
+      uint4 v;
+      uint32_t* pv = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = 16 * q + 8 * h + 2 * e;
+        const float2 z = __fadd2_rn(make_float2(__uint_as_float(r[8 * h + 2 * e]), __uint_as_float(r[8 * h + 2 * e + 1])),
+                                    *reinterpret_cast<const float2*>(bias + k));
+        const float2 a2 = gelu2(z);
+        pv[e] = pack_bf16(a2.x, a2.y);
+      }
+      *reinterpret_cast<uint4*>(a + canon(m, 16 * q + 8 * h, NH)) = v;
     }
-#pragma unroll
-    for (int kc = 0; kc < KC; ++kc) {
-      uint32_t rb[2];
-      wfrag(rb, w, 16 * KC, kc * 16, j * 8);
-      mma16816(acc[0][j], a[0][kc], rb);
-      mma16816(acc[1][j], a[1][kc], rb);
-    }
-  }
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-      a_next[h][kc][0] = pack_bf16(gelu(acc[h][2 * kc][0]), gelu(acc[h][2 * kc][1]));
-      a_next[h][kc][1] = pack_bf16(gelu(acc[h][2 * kc][2]), gelu(acc[h][2 * kc][3]));
-      a_next[h][kc][2] = pack_bf16(gelu(acc[h][2 * kc + 1][0]), gelu(acc[h][2 * kc + 1][1]));
-      a_next[h][kc][3] = pack_bf16(gelu(acc[h][2 * kc + 1][2]), gelu(acc[h][2 * kc + 1][3]));
-    }
-}
-
-// Output layer (8 columns, no activation) on two tiles: o[h] = b4 + h3[h] W4^T.
-__device__ __forceinline__ void dense_out2(const uint32_t (&a)[2][4][4], const __nv_bfloat16* w, const float* b,
-                                           float (&o)[2][4]) {
-  const int t = threadIdx.x & 3;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    o[h][0] = b[2 * t];
-    o[h][1] = b[2 * t + 1];
-    o[h][2] = b[2 * t];
-    o[h][3] = b[2 * t + 1];
-  }
-#pragma unroll
-  for (int kc = 0; kc < 4; ++kc) {
-    uint32_t rb[2];
-    wfrag(rb, w, NH, kc * 16, 0);
-    mma16816(o[0], a[0][kc], rb);
-    mma16816(o[1], a[1][kc], rb);
   }
 }
 
-// Inference: y[n][NO] (FP32) for x[n][NI] (BF16); each warp takes 32 rows (two 16-row tiles) at a time.
-__global__ void __launch_bounds__(128) k_mlp_forward(const __nv_bfloat16* __restrict__ x, int n,
-                                                     const __nv_bfloat16* __restrict__ wb,
-                                                     const float* __restrict__ wf, float* __restrict__ y) {
-  __shared__ SmemWeights s;
-  load_weights(s, wb, wf);
+// Group g issues one layer (K / 16 MMA steps into its 64 TMEM columns) and waits for it; false (for the whole
+// group) if the wait ran out.
+__device__ __forceinline__ bool tc_layer(SmemTc& s, int g, const __nv_bfloat16* w, int K, int N, uint32_t& phase) {
+  lbm::tc::fence_async_smem();
+  lbm::tc::fence_before_sync();
+  group_sync(g);
+  lbm::tc::fence_after_sync();
+  if ((threadIdx.x & (TC_M - 1)) == 0) {
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    const uint32_t a0 = lbm::smem_addr(s.a[g]), b0 = lbm::smem_addr(w);
+    for (int k = 0; k < K / 16; ++k)
+      lbm::tc::mma_bf16(s.tmem + 64u * g, lbm::tc::smem_desc(a0 + 256u * k, 128u, sbo),
+                        lbm::tc::smem_desc(b0 + 256u * k, 128u, sbo), lbm::tc::idesc_bf16_f32(TC_M, N), k > 0);
+    lbm::tc::commit(&s.bar[g]);
+  }
+  const bool ok = group_sync_and(g, lbm::mbar_wait(&s.bar[g], phase));  // every thread of the group waited
+  phase ^= 1u;
+  lbm::tc::fence_after_sync();
+  return ok;
+}
+
+// Block set-up of the tensor-core network: weights and biases into shared memory, the groups' mbarriers and
+// TMEM_COLS columns of tensor memory (64 a group; at most four such blocks fit a SM's shared memory, 512
+// columns).
+__device__ void tc_setup(SmemTc& s, const __nv_bfloat16* wb, const float* wf) {
+  const int t = threadIdx.x;
+  // the four weight matrices as 16-byte vectors (W1 256, W2 and W3 512 each, W4 128 with its padding rows),
+  // every load of a thread issued before its first store: one L2 round trip rather than one per vector
+  constexpr int V1 = NH * NI / 8, V2 = V1 + NH * NH / 8, V3 = V2 + NH * NH / 8, V4 = V3 + TC_NO * NH / 8;
+  constexpr int R = (V4 + TC_G * TC_M - 1) / (TC_G * TC_M);
+  uint4 v[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int j = t + k * TC_G * TC_M;
+    v[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (j < V1) v[k] = __ldg(reinterpret_cast<const uint4*>(wb + OFF_W1) + j);
+    else if (j < V2) v[k] = __ldg(reinterpret_cast<const uint4*>(wb + OFF_W2) + (j - V1));
+    else if (j < V3) v[k] = __ldg(reinterpret_cast<const uint4*>(wb + OFF_W3) + (j - V2));
+    else if (j < V3 + NO * NH / 8) v[k] = __ldg(reinterpret_cast<const uint4*>(wb + OFF_W4) + (j - V3));
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int j = t + k * TC_G * TC_M;
+    if (j < V1) *reinterpret_cast<uint4*>(s.w1 + canon(j / (NI / 8), 8 * (j % (NI / 8)), NI)) = v[k];
+    else if (j < V2) *reinterpret_cast<uint4*>(s.w2 + canon((j - V1) / 8, 8 * ((j - V1) % 8), NH)) = v[k];
+    else if (j < V3) *reinterpret_cast<uint4*>(s.w3 + canon((j - V2) / 8, 8 * ((j - V2) % 8), NH)) = v[k];
+    else if (j < V4) *reinterpret_cast<uint4*>(s.w4 + canon((j - V3) / 8, 8 * ((j - V3) % 8), NH)) = v[k];
+  }
+  for (int k = t; k < NH; k += blockDim.x) {
+    s.b1[k] = wf[OFF_B1 + k];
+    s.b2[k] = wf[OFF_B2 + k];
+    s.b3[k] = wf[OFF_B3 + k];
+  }
+  if (t < NO) s.b4[t] = wf[OFF_B4 + t];
+  if (t == 0) {
+    for (int g = 0; g < TC_G; ++g) lbm::mbar_init(&s.bar[g], 1);
+    lbm::mbar_init_fence();
+  }
+  if ((t >> 5) == 0) lbm::tc::tmem_alloc(&s.tmem, TC_COLS);
+  lbm::tc::fence_before_sync();
   __syncthreads();
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (long long r0 = ((long long)blockIdx.x * nwarps + warp) * 32; r0 < n;
-       r0 += (long long)gridDim.x * nwarps * 32) {
-    uint32_t a0[2][2][4];
+  lbm::tc::fence_after_sync();
+}
+
+// Whole block, after both groups' last use of tensor memory.
+__device__ void tc_teardown(SmemTc& s) {
+  lbm::tc::fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    lbm::tc::fence_after_sync();
+    lbm::tc::tmem_dealloc(s.tmem, TC_COLS);
+    lbm::tc::tmem_relinquish();
+  }
+}
+
+// Group g's four layers on the 128 rows it wrote into s.a[g] (layer-1 input, row m = this thread's); o
+// receives this thread's NO outputs.  Returns false (for the whole group) if a wait on the tensor core ran
+// out, o then NaN.
+__device__ bool tc_network(SmemTc& s, int g, int m, uint32_t& phase, float (&o)[NO]) {
+  // this warp's 32 TMEM lanes (warp w of the group reads lanes 32 w .. 32 w + 31) of the group's columns
+  const uint32_t trow = s.tmem + 64u * g + ((uint32_t)(32 * (m >> 5)) << 16);
+  bool ok = tc_layer(s, g, s.w1, NI, NH, phase);
+  if (ok) tc_hidden_epilogue(s.a[g], trow, s.b1, m);
+  ok = ok && tc_layer(s, g, s.w2, NH, NH, phase);
+  if (ok) tc_hidden_epilogue(s.a[g], trow, s.b2, m);
+  ok = ok && tc_layer(s, g, s.w3, NH, NH, phase);
+  if (ok) tc_hidden_epilogue(s.a[g], trow, s.b3, m);
+  ok = ok && tc_layer(s, g, s.w4, NH, TC_NO, phase);
+  if (ok) {
+    uint32_t r[16];
+    lbm::tc::ld_32x32b_x16(trow, r);
+    lbm::tc::wait_ld();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long ra = r0 + 16 * h + g, rbr = ra + 8;
+    for (int j = 0; j < NO; ++j) o[j] = __uint_as_float(r[j]) + s.b4[j];
+  } else {
 #pragma unroll
-      for (int kc = 0; kc < 2; ++kc) {
-        const int c = kc * 16 + 2 * t;
-        a0[h][kc][0] = ra < n ? *reinterpret_cast<const uint32_t*>(x + ra * NI + c) : 0u;
-        a0[h][kc][1] = rbr < n ? *reinterpret_cast<const uint32_t*>(x + rbr * NI + c) : 0u;
-        a0[h][kc][2] = ra < n ? *reinterpret_cast<const uint32_t*>(x + ra * NI + c + 8) : 0u;
-        a0[h][kc][3] = rbr < n ? *reinterpret_cast<const uint32_t*>(x + rbr * NI + c + 8) : 0u;
-      }
+    for (int j = 0; j < NO; ++j) o[j] = __int_as_float(0x7fc00000);
+  }
+  return ok;
+}
+
+__global__ void __launch_bounds__(TC_G * TC_M, 4) k_mlp_forward_tc(const __nv_bfloat16* __restrict__ x, int n,
+                                                                   const __nv_bfloat16* __restrict__ wb,
+                                                                   const float* __restrict__ wf,
+                                                                   float* __restrict__ y) {
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  SmemTc& s = *reinterpret_cast<SmemTc*>(tc_smem);
+  const int g = threadIdx.x / TC_M, m = threadIdx.x % TC_M;
+  tc_setup(s, wb, wf);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long r0 = ((long long)blockIdx.x * TC_G + g) * TC_M; r0 < n && ok;
+       r0 += (long long)gridDim.x * TC_G * TC_M) {
+    const long long row = r0 + m;
+    // layer-1 input: this thread's row of x (32 BF16 = four 16-byte vectors)
+#pragma unroll
+    for (int c = 0; c < NI / 8; ++c) {
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (row < n) v = __ldg(reinterpret_cast<const uint4*>(x + row * NI + 8 * c));
+      *reinterpret_cast<uint4*>(s.a[g] + canon(m, 8 * c, NI)) = v;
     }
-    uint32_t h1[2][4][4], h2[2][4][4], h3[2][4][4];
-    dense_gelu2<2>(a0, s.w1, s.b1, h1);
-    dense_gelu2<4>(h1, s.w2, s.b2, h2);
-    dense_gelu2<4>(h2, s.w3, s.b3, h3);
-    float o[2][4];
-    dense_out2(h3, s.w4, s.b4, o);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long ra = r0 + 16 * h + g, rbr = ra + 8;
-      if (ra < n) {
-        y[ra * NO + 2 * t] = o[h][0];
-        y[ra * NO + 2 * t + 1] = o[h][1];
-      }
-      if (rbr < n) {
-        y[rbr * NO + 2 * t] = o[h][2];
-        y[rbr * NO + 2 * t + 1] = o[h][3];
-      }
+    float o[NO];
+    ok = tc_network(s, g, m, phase, o);
+    if (row < n) {
+      float4* yo = reinterpret_cast<float4*>(y + row * NO);
+      yo[0] = make_float4(o[0], o[1], o[2], o[3]);
+      yo[1] = make_float4(o[4], o[5], o[6], o[7]);
     }
   }
+  tc_teardown(s);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,22 +648,23 @@ __global__ void __launch_bounds__(128) k_step_closure(const float* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // Fused closure step: features, MLP and the corrected collision of a 32 x 4 tile of cells per block
-// iteration (warp w takes row w of the tile, one cell per lane).  The moments of the tile and its
-// one-cell halo (periodic, as lbm_closure_features) are converted to BF16 features in shared memory
-// once; each warp builds its two 16-cell A fragments from them, runs the layer chain of
-// k_mlp_forward, leaves the three used outputs of its 32 cells in shared memory and then pulls,
-// collides and stores its cells as k_step_closure does.  Same arithmetic in the same order as
-// features + forward + k_step_closure, so the result is bitwise the three-kernel path's.
+// iteration of each of the block's two groups; thread 32 w + l of a group takes the cell in column l of row w
+// of its tile, which is also its row of the network's 128-row tile.  The moments of the tile and its one-cell halo (periodic, as
+// lbm_closure_features) are converted to BF16 features in shared memory once; each thread writes its
+// cell's 27 features as its layer-1 input row, the block runs the tensor-core layer chain of
+// lbm_closure_forward, and each thread pulls, collides and stores its cell as k_step_closure does with its
+// own row of outputs.  Same arithmetic in the same order as features + forward + k_step_closure, so the
+// result is bitwise the three-kernel path's.
 // ---------------------------------------------------------------------------
 constexpr int FT_X = 32, FT_Y = 4;
+static_assert(FT_X * FT_Y == TC_M, "one network tile per cell tile");
 
 struct SmemFused {
-  SmemWeights w;
-  __nv_bfloat16 m[FT_Y + 2][FT_X + 2][3];  // (rho - 1, ux, uy) / u0 of the tile and its halo
-  float y[FT_Y][FT_X][3];
+  SmemTc t;
+  __nv_bfloat16 m[TC_G][FT_Y + 2][FT_X + 2][3];  // (rho - 1, ux, uy) / u0 of each group's tile and its halo
 };
 
-__global__ void __launch_bounds__(128) k_step_closure_fused(const float* __restrict__ fin, float* __restrict__ fout,
+__global__ void __launch_bounds__(TC_G * TC_M, 3) k_step_closure_fused(const float* __restrict__ fin, float* __restrict__ fout,
                                                             lbm::StepGeom g, lbm::CollParams<float> P,
                                                             const double* __restrict__ rho,
                                                             const double* __restrict__ ux,
@@ -551,66 +672,52 @@ __global__ void __launch_bounds__(128) k_step_closure_fused(const float* __restr
                                                             const __nv_bfloat16* __restrict__ wb,
                                                             const float* __restrict__ wf, float scale) {
   using L = lbm::D2Q9;
-  __shared__ SmemFused s;
-  load_weights(s.w, wb, wf);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, t = lane & 3;
+  extern __shared__ __align__(128) unsigned char tc_smem[];
+  SmemFused& s = *reinterpret_cast<SmemFused*>(tc_smem);
+  tc_setup(s.t, wb, wf);
+  const int grp = threadIdx.x / TC_M, m = threadIdx.x % TC_M, lane = m & 31, warp = m >> 5;
+  auto& hm = s.m[grp];
   const int tiles_x = (g.nx + FT_X - 1) / FT_X, tiles_y = (g.ny + FT_Y - 1) / FT_Y;
-  for (long long tile = blockIdx.x; tile < (long long)tiles_x * tiles_y; tile += gridDim.x) {
+  uint32_t phase = 0;
+  bool ok = true;
+  for (long long tile = (long long)blockIdx.x * TC_G + grp; tile < (long long)tiles_x * tiles_y && ok;
+       tile += (long long)gridDim.x * TC_G) {
     const int x0 = (int)(tile % tiles_x) * FT_X, y0 = (int)(tile / tiles_x) * FT_Y;
-    __syncthreads();  // previous tile's features and outputs are no longer read
-    for (int k = threadIdx.x; k < (FT_Y + 2) * (FT_X + 2); k += blockDim.x) {
+    group_sync(grp);  // previous tile's features are no longer read
+    for (int k = m; k < (FT_Y + 2) * (FT_X + 2); k += TC_M) {
       const int hy = k / (FT_X + 2), hx = k - hy * (FT_X + 2);
       int xs = (x0 + hx - 1) % g.nx, ys = (y0 + hy - 1) % g.ny;
       if (xs < 0) xs += g.nx;
       if (ys < 0) ys += g.ny;
       const long long c = (long long)ys * g.nx + xs;
-      s.m[hy][hx][0] = __float2bfloat16((float)((rho[c] - 1.0) * inv_u0));
-      s.m[hy][hx][1] = __float2bfloat16((float)(ux[c] * inv_u0));
-      s.m[hy][hx][2] = __float2bfloat16((float)(uy[c] * inv_u0));
+      hm[hy][hx][0] = __float2bfloat16((float)((rho[c] - 1.0) * inv_u0));
+      hm[hy][hx][1] = __float2bfloat16((float)(ux[c] * inv_u0));
+      hm[hy][hx][2] = __float2bfloat16((float)(uy[c] * inv_u0));
     }
-    __syncthreads();
-    // feature k of the cell in column cx of this warp's row: neighbour k / 3 (row-major over the 3 x 3
-    // stencil), component k % 3; zero beyond the 27 used inputs
-    auto feat = [&](int cx, int k) -> __nv_bfloat16 {
-      if (k >= 27) return __float2bfloat16(0.0f);
-      const int j = k / 3;
-      return s.m[warp + j / 3][cx + j % 3][k - 3 * j];
-    };
-    uint32_t a0[2][2][4];
+    group_sync(grp);
+    // feature k of this thread's cell: neighbour k / 3 (row-major over the 3 x 3 stencil), component k % 3;
+    // zero beyond the 27 used inputs
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ra = h * 16 + gq, rb = ra + 8;
+    for (int c = 0; c < NI / 8; ++c) {
+      uint4 v;
+      uint32_t* pv = reinterpret_cast<uint32_t*>(&v);
 #pragma unroll
-      for (int kc = 0; kc < 2; ++kc) {
-        const int c = kc * 16 + 2 * t;
-        a0[h][kc][0] = pack_raw(feat(ra, c), feat(ra, c + 1));
-        a0[h][kc][1] = pack_raw(feat(rb, c), feat(rb, c + 1));
-        a0[h][kc][2] = pack_raw(feat(ra, c + 8), feat(ra, c + 9));
-        a0[h][kc][3] = pack_raw(feat(rb, c + 8), feat(rb, c + 9));
+      for (int e = 0; e < 4; ++e) {
+        __nv_bfloat16 f2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = 8 * c + 2 * e + h;
+          const int j = k / 3;
+          f2[h] = k < 27 ? hm[warp + j / 3][lane + j % 3][k - 3 * j] : __float2bfloat16(0.0f);
+        }
+        pv[e] = pack_raw(f2[0], f2[1]);
       }
+      *reinterpret_cast<uint4*>(s.t.a[grp] + canon(m, 8 * c, NI)) = v;
     }
-    uint32_t h1[2][4][4], h2[2][4][4], h3[2][4][4];
-    dense_gelu2<2>(a0, s.w.w1, s.w.b1, h1);
-    dense_gelu2<4>(h1, s.w.w2, s.w.b2, h2);
-    dense_gelu2<4>(h2, s.w.w3, s.w.b3, h3);
-    float o[2][4];
-    dense_out2(h3, s.w.w4, s.w.b4, o);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int ra = h * 16 + gq, rb = ra + 8;
-      if (t == 0) {
-        s.y[warp][ra][0] = o[h][0];
-        s.y[warp][ra][1] = o[h][1];
-        s.y[warp][rb][0] = o[h][2];
-        s.y[warp][rb][1] = o[h][3];
-      } else if (t == 1) {
-        s.y[warp][ra][2] = o[h][0];
-        s.y[warp][rb][2] = o[h][2];
-      }
-    }
-    __syncwarp();
+    float o[NO];
+    ok = tc_network(s.t, grp, m, phase, o);
     const int x = x0 + lane, yy = y0 + warp;
-    if (x < g.nx && yy < g.ny) {
+    if (ok && x < g.nx && yy < g.ny) {
       float q[L::Q];
       lbm::sfor<0, L::Q>([&](auto I) {
         constexpr int i = LBM_CI(I);
@@ -619,7 +726,7 @@ __global__ void __launch_bounds__(128) k_step_closure_fused(const float* __restr
         const int ys = lbm::src_coord(yy, cy, g.ny, g.bcy);
         q[i] = fin[(long long)i * g.plane + (long long)ys * g.pitch + xs];
       });
-      const float da[3] = {scale * s.y[warp][lane][0], scale * s.y[warp][lane][1], scale * s.y[warp][lane][2]};
+      const float da[3] = {scale * o[0], scale * o[1], scale * o[2]};
       lbm::collide<L, lbm::COLL_RR, false, false, float, true>(q, P, da);
       lbm::sfor<0, L::Q>([&](auto I) {
         constexpr int i = LBM_CI(I);
@@ -627,6 +734,7 @@ __global__ void __launch_bounds__(128) k_step_closure_fused(const float* __restr
       });
     }
   }
+  tc_teardown(s.t);
 }
 
 struct lbm_closure {
@@ -703,12 +811,21 @@ int lbm_closure_get_weights(lbm_closure* c, float* w, int n) {
 
 int lbm_closure_forward(lbm_closure* c, const void* x, int n, float* y, void* stream) {
   if (!c || !x || !y || n < 0) return LBM_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) return LBM_EINVAL;  // 16-byte rows
   if (n == 0) return LBM_OK;
   cudaSetDevice(c->device);
-  const long long pairs = ((long long)n + 31) / 32;  // 32 rows per warp iteration
-  long long blocks = (pairs + 3) / 4;
-  if (blocks > 4096) blocks = 4096;
-  k_mlp_forward<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)x, n, c->wb, c->w, y);
+  static int sms = 0;
+  if (sms == 0) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemTc)) !=
+            cudaSuccess)
+      return LBM_ECUDA;
+  }
+  // two groups of 128 rows a block at a time, four blocks a SM (the shared memory and TMEM hold four)
+  long long blocks = ((long long)n + TC_G * TC_M - 1) / (TC_G * TC_M);
+  if (blocks > 4LL * sms) blocks = 4LL * sms;
+  k_mlp_forward_tc<<<(unsigned)blocks, TC_G * TC_M, sizeof(SmemTc), (cudaStream_t)stream>>>(
+      (const __nv_bfloat16*)x, n, c->wb, c->w, y);
   return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
@@ -804,14 +921,23 @@ int lbm_step_closure(lbm_ctx* c, lbm_closure* cl, double u0, int n) {
   const lbm::CollParams<float> P = closure_coll_params(c);
   const float scale = (float)(u0 * u0 / (1.0 - 1.0 / c->tau));
   const long long tiles = (long long)((c->p.nx + FT_X - 1) / FT_X) * ((c->p.ny + FT_Y - 1) / FT_Y);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_step_closure_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemFused)) != cudaSuccess)
+      return LBM_ECUDA;
+    attr = true;
+  }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_closure_fused, 128, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_closure_fused, TC_G * TC_M, sizeof(SmemFused)) !=
+          cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  const long long grid = std::min<long long>(tiles, (long long)per_sm * c->g.nsm);
+  if (per_sm > 4) per_sm = 4;  // 128 TMEM columns a block: four blocks hold a SM's 512
+  const long long grid = std::min<long long>((tiles + TC_G - 1) / TC_G, (long long)per_sm * c->g.nsm);
   for (int k = 0; k < n; ++k) {
     if (lbm_moments(c, r, u, v, nullptr, 1) != LBM_OK) return LBM_ECUDA;
-    k_step_closure_fused<<<(unsigned)grid, 128, 0, c->st>>>(
+    k_step_closure_fused<<<(unsigned)grid, TC_G * TC_M, sizeof(SmemFused), c->st>>>(
         static_cast<const float*>(c->buf[c->cur]), static_cast<float*>(c->buf[c->cur ^ 1]), c->g, P, r, u, v,
         1.0 / u0, cl->wb, cl->w, scale);
     if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
