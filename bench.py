@@ -504,6 +504,33 @@ def batched_sweep_bench(stream_t, steps, n=64, storage="f16"):
         lbm.lbm_batch_destroy(b)
 
 
+def closure_forward_bench(stream_t, n=1 << 22, reps=10):
+    """Inference throughput of the closure network alone (lbm_closure_forward, tcgen05) on n rows of seeded
+    random BF16 features with the seeded initial weights: the profiling case of its kernel."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    st = stream_t.cuda_stream
+    cl = lbm.lbm_closure_create()
+    try:
+        lbm.lbm_closure_set_weights(cl, wl.closure_initial_weights(3, out_scale=1.0))
+        g = torch.Generator(device="cuda").manual_seed(5)
+        x = (0.5 * torch.randn((n, lbm.CLOSURE_IN), device="cuda", generator=g)).to(torch.bfloat16)
+        y = torch.empty((n, lbm.CLOSURE_OUT), dtype=torch.float32, device="cuda")
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(3):
+            lbm.lbm_closure_forward(cl, x, n, y, st)
+        e[0].record(stream_t)
+        for _ in range(reps):
+            lbm.lbm_closure_forward(cl, x, n, y, st)
+        e[1].record(stream_t)
+        torch.cuda.synchronize()
+        ms = e[0].elapsed_time(e[1]) / reps
+    finally:
+        lbm.lbm_closure_destroy(cl)
+    flops = 2 * (lbm.CLOSURE_IN * lbm.CLOSURE_HID + 2 * lbm.CLOSURE_HID ** 2 + lbm.CLOSURE_HID * lbm.CLOSURE_OUT)
+    return {"closure_forward": {"rows": n, "ms": round(ms, 4), "tflops": round(flops * n / ms / 1e9, 2)}}
+
+
 def closure_bench(stream_t, fine=1024, factor=8, reynolds=1e5, seeds=4, held_out=3, epochs=20):
     """Learned a1^(2) closure: training data from box-filtered fine D2Q9 RR shear layers, Adam training of the
     BF16 tensor-core MLP, then the coarse grid run from the filtered initial state with and without the
@@ -773,6 +800,8 @@ def main():
     ap.add_argument("--batch-launch", default=None, metavar="THREADS,ROWS,BLOCKS_PER_SM",
                     help="launch shape of --headline-only instead of the autotuner's")
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
+    ap.add_argument("--closure-forward-only", action="store_true",
+                    help="profiling case: only the closure network's inference on 4M random rows")
     ap.add_argument("--d3-only", action="store_true",
                     help="only the 3D lattice section (--grid3, --storage as a comma list, --lattices3)")
     ap.add_argument("--grid3", default="256", help="n (an n^3 grid) or nx,ny,nz of the 3D section")
@@ -810,6 +839,13 @@ def main():
         stream_t = torch.cuda.Stream()
         torch.cuda.set_stream(stream_t)
         print(json.dumps(closure_bench(stream_t, fine=args.closure_fine, reynolds=args.closure_re)))
+        return
+    if args.closure_forward_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream_t = torch.cuda.Stream()
+        torch.cuda.set_stream(stream_t)
+        print(json.dumps(closure_forward_bench(stream_t, reps=max(1, args.steps))))
         return
     if args.d3_only:
         import torch

@@ -182,53 +182,92 @@ struct Step3Pair {
   static constexpr int MIN_BLOCKS = 4;
 };
 
-template <class L, class S>
+// ROWS as for k_step3: interior rows take one base pointer per x-velocity; edge rows (and every row of a grid
+// without the split) the per-population source coordinates (periodic or zero-gradient y and z faces).
+template <class L, class S, int ROWS>
 __global__ void __launch_bounds__(STEP_BX, Step3Pair<L, S>::MIN_BLOCKS)
     k_step3_pair(const S* __restrict__ fin, S* __restrict__ fout, Geom3 g, int nbx, Rows3 rows, CollParams<F2> P,
                  const __grid_constant__ PullOffsets3<L::Q> off) {
   const int rb = blockIdx.x / nbx;
   const int bx = blockIdx.x - rb * nbx;
-  const int z = L::VMAX + rb / rows.ny_in;
-  const int y = L::VMAX + (rb - (rb / rows.ny_in) * rows.ny_in);
+  int y, z;
+  if constexpr (ROWS == ROWS_EDGE) {
+    edge_row<L::VMAX>(g, rb, y, z);
+  } else if constexpr (ROWS == ROWS_INTERIOR) {
+    z = L::VMAX + rb / rows.ny_in;
+    y = L::VMAX + (rb - (rb / rows.ny_in) * rows.ny_in);
+  } else {
+    y = rb % g.ny;
+    z = rb / g.ny;
+  }
   const int x = 2 * (bx * STEP_BX + (int)threadIdx.x);
   if (x >= g.nx) return;  // nx is even: a pair is whole or absent (no barrier below)
   const long long cen = (long long)z * g.plane + (long long)y * g.pitch + x;
-  const char* c = reinterpret_cast<const char*>(fin + cen);
-  // one base pointer per x-velocity and cell, moved by a whole row where x - c_x leaves [0, nx) (periodic x,
-  // nx >= VMAX: one fold); an even c_x moves both cells of the pair together
-  const char* cb0[2 * L::VMAX + 1];
-  const char* cb1[2 * L::VMAX + 1];
-  auto fold = [&](int xs) { return (xs < 0 ? g.nx : 0) - (xs >= g.nx ? g.nx : 0); };
-  sfor<0, 2 * L::VMAX + 1>([&](auto J) {
-    constexpr int j = LBM_CI(J);
-    constexpr int cx = j - L::VMAX;
-    if constexpr (cx == 0) {
-      cb0[j] = c;
-      cb1[j] = c;
-    } else {
-      cb0[j] = c + (long long)fold(x - cx) * (long long)sizeof(S);
-      cb1[j] = (cx % 2 == 0) ? cb0[j] : c + (long long)fold(x + 1 - cx) * (long long)sizeof(S);
-    }
-  });
   char* o = reinterpret_cast<char*>(fout + cen);
-  collide3_rr<L, Store<S>::SHIFTED, F2>(
-      [&](auto I) -> F2 {
-        constexpr int i = LBM_CI(I);
-        constexpr int j = L::CX[i] + L::VMAX;
-        const long long so = off.src[i];
-        if constexpr (L::CX[i] % 2 == 0) {
-          return ld_pair<S>(cb0[j] + so);
-        } else {
-          const float a = ld_raw<S>(cb0[j] + so);
-          const float b = ld_raw<S>(cb1[j] + so + (long long)sizeof(S));
-          return F2(a, b);
-        }
-      },
-      P,
-      [&](auto I, F2 v) {
-        constexpr int i = LBM_CI(I);
-        st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), v);
-      });
+  auto store = [&](auto I, F2 v) {
+    constexpr int i = LBM_CI(I);
+    st_pair<S>(reinterpret_cast<S*>(o + off.dst[i]), v);
+  };
+  if constexpr (ROWS == ROWS_INTERIOR) {
+    const char* c = reinterpret_cast<const char*>(fin + cen);
+    // one base pointer per x-velocity and cell, moved by a whole row where x - c_x leaves [0, nx) (periodic x,
+    // nx >= VMAX: one fold); an even c_x moves both cells of the pair together
+    const char* cb0[2 * L::VMAX + 1];
+    const char* cb1[2 * L::VMAX + 1];
+    auto fold = [&](int xs) { return (xs < 0 ? g.nx : 0) - (xs >= g.nx ? g.nx : 0); };
+    sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+      constexpr int j = LBM_CI(J);
+      constexpr int cx = j - L::VMAX;
+      if constexpr (cx == 0) {
+        cb0[j] = c;
+        cb1[j] = c;
+      } else {
+        cb0[j] = c + (long long)fold(x - cx) * (long long)sizeof(S);
+        cb1[j] = (cx % 2 == 0) ? cb0[j] : c + (long long)fold(x + 1 - cx) * (long long)sizeof(S);
+      }
+    });
+    collide3_rr<L, Store<S>::SHIFTED, F2>(
+        [&](auto I) -> F2 {
+          constexpr int i = LBM_CI(I);
+          constexpr int j = L::CX[i] + L::VMAX;
+          const long long so = off.src[i];
+          if constexpr (L::CX[i] % 2 == 0) {
+            return ld_pair<S>(cb0[j] + so);
+          } else {
+            const float a = ld_raw<S>(cb0[j] + so);
+            const float b = ld_raw<S>(cb1[j] + so + (long long)sizeof(S));
+            return F2(a, b);
+          }
+        },
+        P, store);
+  } else {
+    // source columns per x-velocity (periodic x, even nx: an even c_x keeps the pair together and aligned),
+    // source row and plane per population
+    int xs0[2 * L::VMAX + 1], xs1[2 * L::VMAX + 1];
+    sfor<0, 2 * L::VMAX + 1>([&](auto J) {
+      constexpr int j = LBM_CI(J);
+      constexpr int cx = j - L::VMAX;
+      xs0[j] = src_coord(x, cx, g.nx, BC_PERIODIC);
+      xs1[j] = (cx % 2 == 0) ? xs0[j] + 1 : src_coord(x + 1, cx, g.nx, BC_PERIODIC);
+    });
+    const char* base = reinterpret_cast<const char*>(fin);
+    collide3_rr<L, Store<S>::SHIFTED, F2>(
+        [&](auto I) -> F2 {
+          constexpr int i = LBM_CI(I);
+          constexpr int j = L::CX[i] + L::VMAX;
+          const int ys = src_coord(y, L::CY[i], g.ny, g.bc[1]);
+          const int zs = src_coord(z, L::CZ[i], g.nz, g.bc[2]);
+          const char* row = base + off.dst[i] + ((long long)zs * g.plane + (long long)ys * g.pitch) * (long long)sizeof(S);
+          if constexpr (L::CX[i] % 2 == 0) {
+            return ld_pair<S>(row + (long long)xs0[j] * (long long)sizeof(S));
+          } else {
+            const float a = ld_raw<S>(row + (long long)xs0[j] * (long long)sizeof(S));
+            const float b = ld_raw<S>(row + (long long)xs1[j] * (long long)sizeof(S));
+            return F2(a, b);
+          }
+        },
+        P, store);
+  }
 }
 
 // Staged variant for x-periodic grids whose rows are whole 16-byte units: a persistent block walks row tiles
@@ -460,32 +499,41 @@ inline cudaError_t launch_step3_t(const void* fin, void* fout, const Geom3& g, c
   const int nbx = (g.nx + STEP_BX - 1) / STEP_BX;
   const Rows3 rows = rows3<L::VMAX>(g);
   const CollParams<Real> P = cast_params<Real>(pd);
-  if (rows.interior == 0) {
-    const long long nb = (long long)nbx * g.ny * g.nz;
-    if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_step3<L, COLL, Real, S, ROWS_ALL><<<(unsigned)nb, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, rows, P,
-                                                                        off);
-    return cudaGetLastError();
-  }
-  const long long nb_in = (long long)nbx * rows.interior, nb_edge = (long long)nbx * rows.edge;
-  if (nb_in > 0x7fffffffLL || nb_edge > 0x7fffffffLL) return cudaErrorInvalidValue;
+  // D3Q103 RR with FP32 arithmetic on x-periodic grids of even nx: the two-cell kernel for every row
   bool pairs = false;
   if constexpr (Step3Pair<L, S>::ENABLED && COLL == COLL_RR && sizeof(Real) == 4)
     pairs = g.bc[0] == BC_PERIODIC && g.nx % 2 == 0 && g.nx >= L::VMAX;
+  const int nbx2 = (g.nx + 2 * STEP_BX - 1) / (2 * STEP_BX);
+  if (rows.interior == 0) {
+    const long long nb = (long long)(pairs ? nbx2 : nbx) * g.ny * g.nz;
+    if (nb > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (pairs) {
+      if constexpr (Step3Pair<L, S>::ENABLED && COLL == COLL_RR && sizeof(Real) == 4)
+        k_step3_pair<L, S, ROWS_ALL><<<(unsigned)nb, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx2, rows,
+                                                                      cast_params<F2>(pd), off);
+    } else {
+      k_step3<L, COLL, Real, S, ROWS_ALL><<<(unsigned)nb, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, rows,
+                                                                          P, off);
+    }
+    return cudaGetLastError();
+  }
+  const int nbr = pairs ? nbx2 : nbx;
+  const long long nb_in = (long long)nbr * rows.interior, nb_edge = (long long)nbr * rows.edge;
+  if (nb_in > 0x7fffffffLL || nb_edge > 0x7fffffffLL) return cudaErrorInvalidValue;
   if (pairs) {
     if constexpr (Step3Pair<L, S>::ENABLED && COLL == COLL_RR && sizeof(Real) == 4) {
-      const int nbx2 = (g.nx + 2 * STEP_BX - 1) / (2 * STEP_BX);
-      const long long nb2 = (long long)nbx2 * rows.interior;
-      if (nb2 > 0x7fffffffLL) return cudaErrorInvalidValue;
-      k_step3_pair<L, S><<<(unsigned)nb2, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx2, rows,
-                                                           cast_params<F2>(pd), off);
+      const CollParams<F2> P2 = cast_params<F2>(pd);
+      k_step3_pair<L, S, ROWS_INTERIOR><<<(unsigned)nb_in, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx2,
+                                                                            rows, P2, off);
+      k_step3_pair<L, S, ROWS_EDGE><<<(unsigned)nb_edge, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx2, rows,
+                                                                          P2, off);
     }
   } else {
     k_step3<L, COLL, Real, S, ROWS_INTERIOR><<<(unsigned)nb_in, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
                                                                                   rows, P, off);
+    k_step3<L, COLL, Real, S, ROWS_EDGE><<<(unsigned)nb_edge, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx,
+                                                                              rows, P, off);
   }
-  k_step3<L, COLL, Real, S, ROWS_EDGE><<<(unsigned)nb_edge, STEP_BX, 0, st>>>((const S*)fin, (S*)fout, g, nbx, rows,
-                                                                            P, off);
   return cudaGetLastError();
 }
 
