@@ -82,30 +82,36 @@ __global__ void k_init(const double* __restrict__ rho, const double* __restrict_
 }
 
 // Macroscopic fields of the stored state (Sec. II.A).
-template <class L, class S>
+// One block row of FB columns of one grid row (blockIdx.y, then every gridDim.y-th row): no 64-bit division of
+// the cell index.  The FP64 sums skip the terms whose velocity factor is zero, the energy sum is made only
+// where theta is asked for on a thermal lattice (E2), and u = j * (1 / rho): GB300's FP64 rate makes these
+// the kernel's cost (65536 D2Q9 cells: 12.3 us before).
+template <class L, class S, bool E2>
 __global__ void k_moments(const S* __restrict__ f, StepGeom g, double rho0, double inv_s, int thermal,
                           double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
                           double* __restrict__ theta) {
-  const long long c = (long long)blockIdx.x * FB + threadIdx.x;
-  const long long n = (long long)g.nx * g.ny;
-  if (c >= n) return;
-  const int x = (int)(c % g.nx), y = (int)(c / g.nx);
-  const long long o = (long long)y * g.pitch + x;
-  double r = 0, jx = 0, jy = 0, e2 = 0;
-  sfor<0, L::Q>([&](auto I) {
-    constexpr int i = LBM_CI(I);
-    constexpr double cx = L::CX[i], cy = L::CY[i];
-    const double fi = decode<L, S, i>(f, (long long)i * g.plane + o, rho0, inv_s);
-    r += fi;
-    jx += cx * fi;
-    jy += cy * fi;
-    e2 += (cx * cx + cy * cy) * fi;
-  });
-  const double u = jx / r, v = jy / r;
-  if (rho) rho[c] = r;
-  if (ux) ux[c] = u;
-  if (uy) uy[c] = v;
-  if (theta) theta[c] = thermal ? (e2 / r - u * u - v * v) / (2.0 * L::CS2) : 1.0;
+  const int x = (int)blockIdx.x * FB + (int)threadIdx.x;
+  if (x >= g.nx) return;
+  for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
+    const long long c = (long long)y * g.nx + x;
+    const long long o = (long long)y * g.pitch + x;
+    double r = 0, jx = 0, jy = 0, e2 = 0;
+    sfor<0, L::Q>([&](auto I) {
+      constexpr int i = LBM_CI(I);
+      constexpr double cx = L::CX[i], cy = L::CY[i];
+      const double fi = decode<L, S, i>(f, (long long)i * g.plane + o, rho0, inv_s);
+      r += fi;
+      if constexpr (cx != 0.0) jx += cx * fi;
+      if constexpr (cy != 0.0) jy += cy * fi;
+      if constexpr (E2 && cx * cx + cy * cy != 0.0) e2 += (cx * cx + cy * cy) * fi;
+    });
+    const double ir = 1.0 / r;
+    const double u = jx * ir, v = jy * ir;
+    if (rho) rho[c] = r;
+    if (ux) ux[c] = u;
+    if (uy) uy[c] = v;
+    if (theta) theta[c] = E2 ? (e2 * ir - u * u - v * v) / (2.0 * L::CS2) : 1.0;
+  }
 }
 
 // Population transfer between the stored (padded, encoded) layout and dense doubles, one plane.
@@ -303,7 +309,11 @@ static cudaError_t init_l(int prec, const double* rho, const double* ux, const d
 template <class L, class S>
 static cudaError_t moments_t(const void* f, const StepGeom& g, double rho0, double inv_s, int thermal, double* rho,
                              double* ux, double* uy, double* th, cudaStream_t st) {
-  k_moments<L, S><<<nblk(g), FB, 0, st>>>((const S*)f, g, rho0, inv_s, thermal, rho, ux, uy, th);
+  const dim3 grid((unsigned)((g.nx + FB - 1) / FB), (unsigned)(g.ny < 65535 ? g.ny : 65535));
+  if (th && thermal)
+    k_moments<L, S, true><<<grid, FB, 0, st>>>((const S*)f, g, rho0, inv_s, thermal, rho, ux, uy, th);
+  else
+    k_moments<L, S, false><<<grid, FB, 0, st>>>((const S*)f, g, rho0, inv_s, thermal, rho, ux, uy, th);
   return cudaGetLastError();
 }
 template <class L>
