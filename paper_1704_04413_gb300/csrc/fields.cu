@@ -82,10 +82,35 @@ __global__ void k_init(const double* __restrict__ rho, const double* __restrict_
 }
 
 // Macroscopic fields of the stored state (Sec. II.A).
+// Compensated FP32 sum (Knuth's two-sum of every term, the rounding errors summed alongside): s + c keeps about
+// twice the FP32 precision.  add_scaled takes k x for a small integer k exactly: a power of two scales exactly,
+// another k adds the product's rounding error (fmaf) to c.
+struct CSum32 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  template <int k>
+  __device__ __forceinline__ void add_scaled(float x) {
+    constexpr int a = k < 0 ? -k : k;
+    if constexpr ((a & (a - 1)) == 0) {
+      add((float)k * x);
+    } else {
+      const float p = (float)k * x;
+      c += fmaf((float)k, x, -p);
+      add(p);
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // One block row of FB columns of one grid row (blockIdx.y, then every gridDim.y-th row): no 64-bit division of
 // the cell index.  The FP64 sums skip the terms whose velocity factor is zero, the energy sum is made only
 // where theta is asked for on a thermal lattice (E2), and u = j * (1 / rho): GB300's FP64 rate makes these
-// the kernel's cost (65536 D2Q9 cells: 12.3 us before).
+// the kernel's cost (65536 D2Q9 cells: 12.3 us before).  FP32 storage sums in compensated FP32 (CSum32).
 template <class L, class S, bool E2>
 __global__ void k_moments(const S* __restrict__ f, StepGeom g, double rho0, double inv_s, int thermal,
                           double* __restrict__ rho, double* __restrict__ ux, double* __restrict__ uy,
@@ -96,15 +121,32 @@ __global__ void k_moments(const S* __restrict__ f, StepGeom g, double rho0, doub
     const long long c = (long long)y * g.nx + x;
     const long long o = (long long)y * g.pitch + x;
     double r = 0, jx = 0, jy = 0, e2 = 0;
-    sfor<0, L::Q>([&](auto I) {
-      constexpr int i = LBM_CI(I);
-      constexpr double cx = L::CX[i], cy = L::CY[i];
-      const double fi = decode<L, S, i>(f, (long long)i * g.plane + o, rho0, inv_s);
-      r += fi;
-      if constexpr (cx != 0.0) jx += cx * fi;
-      if constexpr (cy != 0.0) jy += cy * fi;
-      if constexpr (E2 && cx * cx + cy * cy != 0.0) e2 += (cx * cx + cy * cy) * fi;
-    });
+    if constexpr (std::is_same<S, float>::value && !E2) {
+      // FP32 populations summed exactly enough in compensated FP32 (about 1e-14 relative): FP32 work instead of
+      // FP64, whose rate on GB300 made these sums the pass's cost
+      CSum32 sr, sx, sy;
+      sfor<0, L::Q>([&](auto I) {
+        constexpr int i = LBM_CI(I);
+        constexpr int cx = L::CX[i], cy = L::CY[i];
+        const float fi = __ldg(f + (long long)i * g.plane + o);
+        sr.add(fi);
+        if constexpr (cx != 0) sx.add_scaled<cx>(fi);
+        if constexpr (cy != 0) sy.add_scaled<cy>(fi);
+      });
+      r = sr.value();
+      jx = sx.value();
+      jy = sy.value();
+    } else {
+      sfor<0, L::Q>([&](auto I) {
+        constexpr int i = LBM_CI(I);
+        constexpr double cx = L::CX[i], cy = L::CY[i];
+        const double fi = decode<L, S, i>(f, (long long)i * g.plane + o, rho0, inv_s);
+        r += fi;
+        if constexpr (cx != 0.0) jx += cx * fi;
+        if constexpr (cy != 0.0) jy += cy * fi;
+        if constexpr (E2 && cx * cx + cy * cy != 0.0) e2 += (cx * cx + cy * cy) * fi;
+      });
+    }
     const double ir = 1.0 / r;
     const double u = jx * ir, v = jy * ir;
     if (rho) rho[c] = r;
