@@ -531,6 +531,33 @@ def closure_forward_bench(stream_t, n=1 << 22, reps=10):
     return {"closure_forward": {"rows": n, "ms": round(ms, 4), "tflops": round(flops * n / ms / 1e9, 2)}}
 
 
+def closure_step_bench(stream_t, n=256, steps=200):
+    """The fused closure step alone (lbm_step_closure: moments pass + tensor-core network + corrected
+    collision) on an n^2 D2Q9 shear layer with the seeded initial weights: the profiling case of its kernels."""
+    import torch
+    from paper_1704_04413_gb300 import lbm
+    st = stream_t.cuda_stream
+    u0 = 0.05
+    c = lbm.lbm_create(lbm.make_params("D2Q9", n, n, tau=0.51, collision="rr", hermite_order=2, storage="f32",
+                                       stream=st))
+    cl = lbm.lbm_closure_create()
+    try:
+        lbm.lbm_closure_set_weights(cl, wl.closure_initial_weights(3, out_scale=0.1))
+        fl = wl.double_shear_layer(n, u0)
+        lbm.lbm_init(c, fl.rho, fl.ux, fl.uy, None, fl.grad_u)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        lbm.lbm_step_closure(c, cl, u0, 3)
+        e[0].record(stream_t)
+        lbm.lbm_step_closure(c, cl, u0, steps)
+        e[1].record(stream_t)
+        torch.cuda.synchronize()
+        ms = e[0].elapsed_time(e[1]) / steps
+    finally:
+        lbm.lbm_closure_destroy(cl)
+        lbm.lbm_destroy(c)
+    return {"closure_step": {"grid": n, "us_per_step": round(1000 * ms, 2), "glups": round(n * n / ms / 1e6, 3)}}
+
+
 def closure_bench(stream_t, fine=1024, factor=8, reynolds=1e5, seeds=4, held_out=3, epochs=20):
     """Learned a1^(2) closure: training data from box-filtered fine D2Q9 RR shear layers, Adam training of the
     BF16 tensor-core MLP, then the coarse grid run from the filtered initial state with and without the
@@ -802,6 +829,8 @@ def main():
     ap.add_argument("--closure-only", action="store_true", help="only the learned-closure section")
     ap.add_argument("--closure-forward-only", action="store_true",
                     help="profiling case: only the closure network's inference on 4M random rows")
+    ap.add_argument("--closure-step-only", action="store_true",
+                    help="profiling case: only the fused closure step on a 256^2 grid (--steps steps)")
     ap.add_argument("--d3-only", action="store_true",
                     help="only the 3D lattice section (--grid3, --storage as a comma list, --lattices3)")
     ap.add_argument("--grid3", default="256", help="n (an n^3 grid) or nx,ny,nz of the 3D section")
@@ -839,6 +868,13 @@ def main():
         stream_t = torch.cuda.Stream()
         torch.cuda.set_stream(stream_t)
         print(json.dumps(closure_bench(stream_t, fine=args.closure_fine, reynolds=args.closure_re)))
+        return
+    if args.closure_step_only:
+        import torch
+        torch.cuda.set_device(0)
+        stream_t = torch.cuda.Stream()
+        torch.cuda.set_stream(stream_t)
+        print(json.dumps(closure_step_bench(stream_t, steps=max(1, args.steps))))
         return
     if args.closure_forward_only:
         import torch
