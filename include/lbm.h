@@ -277,7 +277,8 @@ void lbm_closure_destroy(lbm_closure *cl);
 int lbm_closure_set_weights(lbm_closure *cl, const float *w_host, int n);
 int lbm_closure_get_weights(lbm_closure *cl, float *w_host, int n);
 /* y[n][OUT] = MLP(x[n][IN]) on `stream` (device buffers, both 16-byte aligned, else LBM_EINVAL), on the
- * 5th-generation tensor core (tcgen05 MMAs into tensor memory, 128 rows at a time). */
+ * 5th-generation tensor core (tcgen05 MMAs into tensor memory, 128 rows at a time).  Every wait on the tensor
+ * core is bounded (1 s); a wait that ran out leaves NaN in the rows it did not finish. */
 int lbm_closure_forward(lbm_closure *cl, const void *x, int n, float *y, void *stream);
 /* One Adam step (lr, beta1 0.9, beta2 0.999) on the mean squared error of the 3 used outputs over
  * the n samples (x, y_target[n][OUT]); *loss_host (may be NULL) receives the loss before the step. */

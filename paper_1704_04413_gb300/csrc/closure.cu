@@ -813,18 +813,45 @@ int lbm_closure_get_weights(lbm_closure* c, float* w, int n) {
   return cudaMemcpy(w, c->w, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
+// Once per device (the current one): its SM count, the dynamic shared-memory limits and the largest shared-memory
+// carveout of the two tensor-core kernels, and how many fused-step blocks a SM holds (by its shared memory, at most
+// four: 128 TMEM columns a block).  The occupancy calculator gave one block a SM for the fused step, whose
+// launches then ran two tile pairs a block in turn (ncu: 152 blocks, 8 warps a SM).
+static int tc_device_setup(int* sms, int* fused_per_sm) {
+  static int cached_dev = -1, cached_sms = 0, cached_fused = 1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+  if (dev != cached_dev) {
+    int s = 0, smem_sm = 0, reserved = 0;
+    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemTc)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaFuncSetAttribute(k_step_closure_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemFused)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_step_closure_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      return LBM_ECUDA;
+    const int fit = smem_sm / ((int)sizeof(SmemFused) + reserved);
+    cached_fused = fit < 1 ? 1 : (fit > 4 ? 4 : fit);
+    cached_sms = s;
+    cached_dev = dev;
+  }
+  *sms = cached_sms;
+  if (fused_per_sm) *fused_per_sm = cached_fused;
+  return LBM_OK;
+}
+
 int lbm_closure_forward(lbm_closure* c, const void* x, int n, float* y, void* stream) {
   if (!c || !x || !y || n < 0) return LBM_EINVAL;
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) return LBM_EINVAL;  // 16-byte rows
   if (n == 0) return LBM_OK;
-  cudaSetDevice(c->device);
-  static int sms = 0;
-  if (sms == 0) {
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
-        cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmemTc)) !=
-            cudaSuccess)
-      return LBM_ECUDA;
-  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ECUDA;
+  int sms = 0;
+  if (tc_device_setup(&sms, nullptr) != LBM_OK) return LBM_ECUDA;
   // two groups of 128 rows a block at a time, four blocks a SM (the shared memory and TMEM hold four)
   long long blocks = ((long long)n + TC_G * TC_M - 1) / (TC_G * TC_M);
   if (blocks > 4LL * sms) blocks = 4LL * sms;
@@ -925,20 +952,9 @@ int lbm_step_closure(lbm_ctx* c, lbm_closure* cl, double u0, int n) {
   const lbm::CollParams<float> P = closure_coll_params(c);
   const float scale = (float)(u0 * u0 / (1.0 - 1.0 / c->tau));
   const long long tiles = (long long)((c->p.nx + FT_X - 1) / FT_X) * ((c->p.ny + FT_Y - 1) / FT_Y);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_step_closure_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SmemFused)) != cudaSuccess)
-      return LBM_ECUDA;
-    attr = true;
-  }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_closure_fused, TC_G * TC_M, sizeof(SmemFused)) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  if (per_sm > 4) per_sm = 4;  // 128 TMEM columns a block: four blocks hold a SM's 512
-  const long long grid = std::min<long long>((tiles + TC_G - 1) / TC_G, (long long)per_sm * c->g.nsm);
+  int sms = 0, per_sm = 1;
+  if (tc_device_setup(&sms, &per_sm) != LBM_OK) return LBM_ECUDA;
+  const long long grid = std::min<long long>((tiles + TC_G - 1) / TC_G, (long long)per_sm * sms);
   for (int k = 0; k < n; ++k) {
     if (lbm_moments(c, r, u, v, nullptr, 1) != LBM_OK) return LBM_ECUDA;
     k_step_closure_fused<<<(unsigned)grid, TC_G * TC_M, sizeof(SmemFused), c->st>>>(
