@@ -126,7 +126,9 @@ int lbm_init(lbm_ctx *c, const double *rho, const double *ux, const double *uy, 
 int lbm_step(lbm_ctx *c, int n);
 
 /* Macroscopic fields of the current state: rho, ux, uy and theta
- * (theta = 1 when isothermal); any output may be NULL. */
+ * (theta = 1 when isothermal); any output may be NULL.  Double precision: FP64 sums of
+ * the populations, except FP32 storage, whose populations are summed in compensated
+ * FP32 (about twice the FP32 precision, 1e-14 relative). */
 int lbm_moments(lbm_ctx *c, double *rho, double *ux, double *uy, double *theta, int on_device);
 
 /* FP64 domain sums: out[0] mass, out[1..2] momentum, out[3] total energy
@@ -297,8 +299,9 @@ int lbm_closure_coarsen(const double *rho, const double *ux, const double *uy, i
                         double u0, double *rho_c, double *ux_c, double *uy_c, float *y, void *stream);
 /* n RR steps of a D2Q9 FP32 context whose a1^(2) gets the closure's correction
  * Delta a1 = u0^2 y / (1 - 1/tau), y predicted each step from the current fields.  Two launches per
- * step (the FP64 moments, then features + network + collision fused per tile of cells); the result is
- * bitwise that of lbm_moments + lbm_closure_features + lbm_closure_forward + lbm_closure_apply.
+ * step (the moments, then features + network + collision fused per tile of 128 cells, the network on the
+ * tensor core as in lbm_closure_forward); the result is bitwise that of lbm_moments +
+ * lbm_closure_features + lbm_closure_forward + lbm_closure_apply.
  * Allocates a work area of 96 B per cell on first use.  LBM_EINVAL unless the context is D2Q9, RR,
  * isothermal, FP32 storage, a1 by projection. */
 int lbm_step_closure(lbm_ctx *c, lbm_closure *cl, double u0, int n);
