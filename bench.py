@@ -286,6 +286,23 @@ def e2e_bench(args, st, stream_t):
                     "lbm_moments(pinned host) every step"}
 
 
+def job_time_ms(total_ms, world, device="cuda"):
+    """Time of the whole job's timed region: the maximum over ranks (each rank timed its own region between
+    barriers); one rank: its own time."""
+    if world == 1:
+        return total_ms
+    import torch
+    torch.distributed.barrier()
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_glups(cells_per_step, steps, world, total_ms):
+    """Whole-job throughput: the cells every rank updated over the job's time (replicas: each rank the same)."""
+    return cells_per_step * steps * world / (total_ms * 1e-3) / 1e9
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1704_04413_gb300 import lbm
@@ -306,15 +323,11 @@ def run_ours(args, rank, world, local_rank):
     with Clocks(local_rank) as clk:
         total_ms, window = timed_batch_steps(b, args.steps, args.warmup, stream_t)
         clk.mark(*window)
-    if world > 1:
-        torch.distributed.barrier()
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_time_ms(total_ms, world)
     threads, rows, bps = lbm.lbm_batch_get_launch(b)
     lbm.lbm_batch_destroy(b)
     ms_per_step = total_ms / args.steps
-    value = len(LATTICES) * ncell * args.steps * world / (total_ms * 1e-3) / 1e9
+    value = job_glups(len(LATTICES) * ncell, args.steps, world, total_ms)
     # dominant (and only) kernel of the timed region: the batched step, one launch per step
     dom_bytes = sum(2 * V * BYTES["f32"] * ncell for V in (9, 17, 37))
     achieved = dom_bytes / (ms_per_step * 1e-3) / 1e9
