@@ -265,3 +265,28 @@ def test_d3q103_pair_kernel_interior_rows(storage, tol):
         w = L.w[:, None]
         dev = np.abs(ref / w - 1.0).max()
         assert np.max(np.abs(out - ref) / w) <= tol * dev
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_d3q103_pair_kernel_zero_gradient_faces(storage):
+    """D3Q103 RR with zero-gradient y and z faces and a periodic x of even nx runs the two-cell kernel with
+    per-population source rows (the clamped source rule of both faces): one step against the oracle."""
+    name = "D3Q103"
+    nz, ny, nx = 9, 8, 36
+    f = random_state(name, (nz, ny, nx), 17)
+    bc = (0, 1, 1)
+    with Ctx3(name, nx, ny, nz, 0.62, "rr", 2, 0, storage, bc) as c:
+        c.set_oracle_f(f)
+        pre = c.get_oracle_f()
+        c.m.lbm3_step(c.ctx, 1)
+        got = c.get_oracle_f()
+    p = o.Params3(name, nx, ny, nz, 0.62, "rr", hermite_order=2, bc=bc)
+    ref = o.step(p, pre)
+    L = o.lattice(name)
+    if storage == "f32":
+        e_pop, e_big = coll_errors(got, ref, L.w)
+        assert e_pop <= 2e-6, "pop_rel %.3e max_rel(|f| >= w/10) %.3e" % (e_pop, e_big)
+    else:
+        w = L.w[:, None, None, None]
+        dev = np.abs(ref / w - 1.0).max()
+        assert np.max(np.abs(got - ref) / w) <= 2e-3 * dev
